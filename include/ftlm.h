@@ -1,0 +1,265 @@
+/*
+ * ftlm.h — C ABI of the GB300 symmetry-adapted FTLM library.
+ *
+ * The library evaluates the matrix-free Hamiltonian action H·v of the
+ * isotropic spin-s Heisenberg model (Eq. 1 of arXiv 2607.17429) in the basis
+ * adapted to one S^z sector M and one real irrep Gamma of a site-permutation
+ * group G (Sections 2.3-2.4, Eqs. 8-16), and runs the finite-temperature
+ * Lanczos method on top of it (Section 2.2, Eqs. 4-7 and 14).
+ *
+ * Conventions used by every entry point:
+ *  - Group elements are site permutations, gens[g*n_sites + k] = pi_g(k): the
+ *    digit of site k moves to site pi_g(k) (Section 2.3), U(g)U(h) = U(gh).
+ *    Elements are kept in canonical order: lexicographic order of the arrays
+ *    (pi_g(0), ..., pi_g(N-1)); the identity is element 0.
+ *  - Irreps are real orthogonal (Frobenius-Schur indicator +1, Section 3),
+ *    ordered by dimension, then by character vector (canonical element order,
+ *    rounded to 1e-8) descending; irrep 0 is the trivial irrep.
+ *  - Spin and magnetisation are passed doubled: two_s = 2s, two_M = 2M.
+ *  - Product states are stored packed, ceil(log2(2s+1)) bits per site with
+ *    site k in the k-th bit field; this preserves the order of the paper's
+ *    base-(2s+1) labels (Eq. 2), so orbit representatives (smallest label of
+ *    the orbit, Section 2.3) are the same states.
+ *  - Block vectors are row-major [dim][B]: row (r, k) of the block (k-th
+ *    basis vector of representative r, Eq. 12 at partner row 1), B right-hand
+ *    sides contiguous per row.  Rows follow the representatives in ascending
+ *    label order, k = 0..n_Gamma(r)-1 (Eq. 13).
+ *  - The caller owns every pointer it passes; the library owns opaque handles
+ *    until the matching *_free.  Device pointers must stay valid until the
+ *    work queued on the caller's stream has finished.
+ *  - Every call returns an ftlm_status; on failure ftlm_last_error() gives a
+ *    message (thread-local).  No call aborts, exits or traps on the device.
+ *  - cuda_stream is a cudaStream_t (NULL = the legacy default stream).
+ */
+#ifndef FTLM_H
+#define FTLM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FTLM_OK = 0,
+    FTLM_EINVAL = 1,       /* bad argument (null pointer, out-of-range index or size) */
+    FTLM_ENOTGROUP = 2,    /* generators are not permutations or close to a group above the size limit */
+    FTLM_EBONDS = 3,       /* the bond list is not invariant under every group element (Section 3) */
+    FTLM_EIRREP = 4,       /* irrep construction or verification failed (Section 3) */
+    FTLM_EUNSUPPORTED = 5, /* d_Gamma > 5, complex/quaternionic irrep, |G| > 128 on the GPU path, labels > 64 bits */
+    FTLM_ENOMEM = 6,       /* device or host allocation failed */
+    FTLM_ECUDA = 7,        /* a CUDA runtime call failed */
+    FTLM_ETIMEOUT = 8,     /* a bounded device-side wait gave up */
+    FTLM_EINTERNAL = 9     /* a device bounds check tripped (e.g. a representative missing from the table) */
+} ftlm_status;
+
+typedef enum { FTLM_F64 = 0, FTLM_F32 = 1 } ftlm_dtype; /* vector storage and H·v arithmetic */
+typedef enum { FTLM_GAUSS = 0, FTLM_RADEMACHER = 1 } ftlm_rng;
+
+typedef struct ftlm_group ftlm_group;   /* host: permutations, multiplication table, irreps, bonds */
+typedef struct ftlm_sector ftlm_sector; /* device: representatives, stabilizers, lookup index of one (s, M) */
+typedef struct ftlm_basis ftlm_basis;   /* device: one (s, M, Gamma) block on top of a sector */
+
+/* ---------------------------------------------------------------- group (host) */
+
+/*
+ * Close site-permutation generators into the group and compute its real irreps
+ * (Section 3: closure, irreps from the regular representation, real form,
+ * verification of unitarity, character orthogonality and sum d^2 = |G|).
+ *   n_sites        number of sites N (1..64)
+ *   gens           [n_gens][n_sites] host, gens[g][k] = pi_g(k)
+ *   bonds          [n_bonds][2] host, site pairs of Eq. 1 (i != j)
+ *   J              exchange constant of Eq. 1
+ *   out            receives the new handle
+ * Errors: FTLM_EINVAL, FTLM_ENOTGROUP (not permutations, or |G| > 4096),
+ *         FTLM_EBONDS (Section 3's bond-invariance check), FTLM_EIRREP.
+ * Irreps of complex or quaternionic type are listed (fs = 0 or -1) without
+ * matrices; blocks of such irreps return FTLM_EUNSUPPORTED.
+ */
+ftlm_status ftlm_group_init(int n_sites, int n_gens, const int32_t *gens, int n_bonds, const int32_t *bonds,
+                            double J, ftlm_group **out);
+
+/*
+ * Built-in clusters (Section 3's providers), built from coordinates with
+ * nearest-neighbour bonds and J = 1: "icosahedron", "dodecahedron",
+ * "icosidodecahedron" (I_h, 120), "cuboctahedron" (O_h, 48), "tetrahedron"
+ * (T_d, 24), "dimer", "ring:N" (D_N), "square:LXxLY[:c4v|c2v|t]" (periodic
+ * square lattice with its point group and translations, or translations only).
+ */
+ftlm_status ftlm_group_builtin(const char *name, ftlm_group **out);
+
+/*
+ * Group facts.  Any output pointer may be NULL.
+ *   dims, fs: [n_irreps];  chars: [n_irreps][order] (canonical element order).
+ */
+ftlm_status ftlm_group_info(const ftlm_group *g, int *n_sites, int *order, int *n_irreps, int *dims, int *fs,
+                            double *chars);
+
+/*
+ * Export one irrep and the element table.  rho: [order][d][d] host,
+ * rho[g][a][b] = rho_Gamma(g)_{ab} (NULL to skip; FTLM_EUNSUPPORTED for irreps
+ * without real matrices).  perms: [order][n_sites] (NULL to skip).
+ * bonds: [n_bonds][2] (NULL to skip), n_bonds/J may be NULL.
+ */
+ftlm_status ftlm_group_irrep(const ftlm_group *g, int irrep, double *rho, int32_t *perms);
+ftlm_status ftlm_group_bonds(const ftlm_group *g, int *n_bonds, int32_t *bonds, double *J);
+
+/*
+ * Replace the computed irreps by tabulated ones (Section 2.3: irrep matrices
+ * "from standard tables or computed numerically").  rho_all holds, irrep after
+ * irrep, [order][dims[i]][dims[i]] real matrices in canonical element order.
+ * Every irrep must be a homomorphism with orthogonal matrices, the characters
+ * must be orthonormal and sum d^2 = |G| (Section 3's checks, 1e-9); otherwise
+ * FTLM_EIRREP and the group is unchanged.  The irreps are re-sorted into the
+ * canonical irrep order.  Sectors and blocks built before the call are unaffected.
+ */
+ftlm_status ftlm_group_set_irreps(ftlm_group *g, int n_irreps, const int *dims, const double *rho_all);
+
+void ftlm_group_free(ftlm_group *g);
+
+/* ---------------------------------------------------------------- basis (device) */
+
+/*
+ * Irrep-independent preparation of one S^z sector (Section 3's first phase):
+ * enumerate the sector on the GPU (digit sum N s + M, Section 2.1), keep the
+ * orbit representatives (smallest label, Section 2.3) in ascending order, their
+ * stabilizers (Eq. 8) and a bucket index for label lookup.  Queued on
+ * cuda_stream; the call synchronises that stream before returning.
+ * The sector keeps a copy of the group; the group may be freed afterwards.
+ * Errors: FTLM_EINVAL (M out of range, N s + M not an integer),
+ *         FTLM_EUNSUPPORTED (N * bits > 64, |G| > 128, more than 2^32 - 1
+ *         representatives), FTLM_ENOMEM, FTLM_ECUDA.
+ */
+ftlm_status ftlm_build_sector(const ftlm_group *g, int two_s, int two_M, void *cuda_stream, ftlm_sector **out);
+ftlm_status ftlm_sector_info(const ftlm_sector *s, uint64_t *n_reps, uint64_t *sector_dim, size_t *device_bytes);
+/* labels: [n_reps] packed labels; stab_mask: [n_reps][2] bit g of the 128-bit mask set when g fixes r. */
+ftlm_status ftlm_sector_export(const ftlm_sector *s, uint64_t *labels, uint64_t *stab_mask);
+void ftlm_sector_free(ftlm_sector *s);
+
+/*
+ * Irrep-dependent preparation (Section 3's second phase): per stabilizer
+ * subgroup n_Gamma (Section 2.3), V_r (Eq. 11: modified Gram-Schmidt over the
+ * columns of (1/|Stab|) sum_h rho(h) in column order, residual threshold 1e-8,
+ * count checked against the character formula) and sqrt|Stab|; per
+ * representative the row offset (prefix sum of n_Gamma, Eq. 13).
+ * The block keeps the sector alive (reference counted).
+ * Errors: FTLM_EINVAL (irrep index), FTLM_EUNSUPPORTED (d_Gamma > 5 or no real
+ * matrices), FTLM_EIRREP, FTLM_ENOMEM, FTLM_ECUDA.
+ */
+ftlm_status ftlm_build_block(const ftlm_sector *s, int irrep, void *cuda_stream, ftlm_basis **out);
+
+/* ftlm_build_sector followed by ftlm_build_block; the basis owns its sector. */
+ftlm_status ftlm_build_basis(const ftlm_group *g, int two_s, int two_M, int irrep, void *cuda_stream,
+                             ftlm_basis **out);
+ftlm_status ftlm_basis_info(const ftlm_basis *b, uint64_t *n_reps, uint64_t *dim, size_t *device_bytes);
+/*
+ * Host copies for bit-exact tests (NULL = skip): labels [n_reps] packed,
+ * stab_mask [n_reps][2], n_gamma [n_reps], offsets [n_reps + 1].
+ */
+ftlm_status ftlm_basis_export(const ftlm_basis *b, uint64_t *labels, uint64_t *stab_mask, uint8_t *n_gamma,
+                              uint64_t *offsets);
+void ftlm_basis_free(ftlm_basis *b);
+
+/* ---------------------------------------------------------------- H·v (device) */
+
+/*
+ * y = H x in the (M, Gamma) block, B right-hand sides (1 <= B <= 32), one
+ * launch on cuda_stream, asynchronous.  Per representative r (Eqs. 15-16 in
+ * their Hermitian-transposed pull form):
+ *   y[r,k] = J sum_<ij> m_i m_j x[r,k]
+ *          + sum_{bond, sign} c_a sqrt(|Stab r'|/|Stab r|) [V_r^T rho(g_e) V_r' x_r']_k
+ * where a is the flipped state (Eq. 3 gives c_a), r' = min O(a) and
+ * a = U(g_e) r' are found by the in-kernel representative search, and r' is
+ * looked up in the sorted representative table.
+ *   x, y  device [dim][B] of double (FTLM_F64) or float (FTLM_F32), not aliased.
+ * Errors: FTLM_EINVAL (null pointers, B out of range), FTLM_ECUDA (launch).
+ * A representative missing from the table (impossible for a consistent basis)
+ * sets a device flag reported as FTLM_EINTERNAL by ftlm_basis_check.
+ */
+ftlm_status ftlm_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y, void *cuda_stream);
+
+/* Synchronise cuda_stream and report (then clear) the basis's device error flag. */
+ftlm_status ftlm_basis_check(const ftlm_basis *b, void *cuda_stream);
+
+/* ---------------------------------------------------------------- Lanczos / FTLM */
+
+/*
+ * R independent Lanczos chains on the block (Section 2.2), batched through one
+ * H·v launch per step (at most 32 chains per batch).  Start vectors:
+ * Philox4x32-10 with key (low 32 bits of seed, low 32 bits of block_id) and
+ * counter (row low, row high, chain, 0); Gaussian by Box-Muller on two 53-bit
+ * uniforms, or Rademacher +-1 from bit 0; each chain normalised in FP64.
+ * Recurrence: w = H v_j; alpha_j = <v_j, w>; w -= alpha_j v_j + beta_j v_{j-1};
+ * beta_{j+1} = |w|; v_{j+1} = w / beta_{j+1}; dot products and norms
+ * accumulated in FP64 from the stored values (FP32 vectors in FTLM_F32).
+ * A chain stops after step j when beta_{j+1} <= tol (|alpha_j| + beta_j)
+ * (tol = 1e-12 for FP64, 1e-6 for FP32) or when j + 1 = min(n_steps, dim).
+ *   alpha, beta   host [R][n_steps]; beta[r][j] = beta_{j+1} (beta[r][m-1] is
+ *                 the final residual norm); entries past steps_done are 0.
+ *   steps_done    host [R].
+ * Device work memory (3 [dim][B] vectors and reduction scratch) is allocated
+ * and freed by the call.  Synchronises cuda_stream before returning.
+ */
+ftlm_status ftlm_lanczos(const ftlm_basis *b, ftlm_dtype dtype, int R, int n_steps, uint64_t seed,
+                         uint64_t block_id, ftlm_rng rng, void *cuda_stream, double *alpha, double *beta,
+                         int *steps_done);
+
+/*
+ * Ritz values and weights of tridiagonal matrices on the GPU in FP64 (implicit
+ * QL with Wilkinson shifts, first eigenvector row only; Section 2.2).
+ *   n_chains, m[c] = steps of chain c, alpha/beta host [n_chains][ld];
+ *   theta, w: host [n_chains][ld] (entries past m[c] set to 0).
+ */
+ftlm_status ftlm_ritz(int n_chains, int ld, const int *m, const double *alpha, const double *beta, double *theta,
+                      double *w, void *cuda_stream);
+
+typedef struct {
+    int two_M;              /* 2M of the block's sector */
+    int d_gamma;            /* irrep dimension (Eq. 14 weight) */
+    uint64_t dim;           /* block dimension D_{M,Gamma} (Eq. 13) */
+    int R;                  /* number of chains */
+    int ld;                 /* leading dimension of alpha/beta (>= max steps) */
+    const int *steps_done;  /* [R] */
+    const double *alpha;    /* [R][ld] */
+    const double *beta;     /* [R][ld] */
+} ftlm_block;
+
+/*
+ * FTLM thermal sums over all blocks on the GPU in FP64 (Eqs. 5-7 with the
+ * weight mult_M d_Gamma D/R of Eq. 14; mult_M = 2 for M > 0, 1 for M = 0;
+ * k_B = mu_B = 1).  Ritz pairs from ftlm_ritz's method; exponentials shifted
+ * by the global minimum Ritz value E0.  C = beta^2 <(H - <H>)^2> (centred),
+ * chi = g^2 beta sum mult_M M^2 Z_M / sum mult_M Z_M.
+ *   T: host [n_T] (> 0); outputs lnZ, E, C, chi host [n_T] (any may be NULL),
+ *   E0 host [1] (may be NULL).  Synchronises cuda_stream.
+ */
+ftlm_status ftlm_thermo(int n_blocks, const ftlm_block *blocks, int n_T, const double *T, double g, double *lnZ,
+                        double *E, double *C, double *chi, double *E0, void *cuda_stream);
+
+/* ---------------------------------------------------------------- profiling */
+
+/*
+ * Library-wide counters (tracing support; no counterpart in the paper beyond
+ * its wall times).  kernel_launches counts every kernel the library launched
+ * since the last reset.  While profiling is enabled, every H·v launch is
+ * bracketed by CUDA events on its stream; hv_ms is their summed device time
+ * and hv_rows the summed dim * B.  ftlm_profile_get waits for pending events.
+ */
+typedef struct {
+    uint64_t kernel_launches;
+    uint64_t hv_launches;
+    double hv_ms;
+    uint64_t hv_rows;
+} ftlm_profile;
+ftlm_status ftlm_profile_enable(int on);
+ftlm_status ftlm_profile_reset(void);
+ftlm_status ftlm_profile_get(ftlm_profile *out);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *ftlm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FTLM_H */

@@ -127,3 +127,56 @@ class BlockBasis:
 def block(group, bonds, two_s, two_M, irrep, J=1.0, sector=None):
     sec = sector if sector is not None else SectorBasis(group, two_s, two_M)
     return BlockBasis(sec, irrep).with_hamiltonian(bonds, J)
+
+
+def hv_rows_by_label(group, irrep, bonds, J, two_s, rep_labels, xvals):
+    """Rows of y = H x for the given representatives, without a representative table.
+
+    rep_labels: base-(2s+1) labels of orbit representatives.  xvals(label, n)
+    returns the [n, B] block-vector rows of representative ``label``.  Every
+    quantity is computed from the label itself: the off-diagonal terms of the
+    representative (flipped label, its orbit minimum r' and g*, c_a of Eq. 3),
+    the stabilizers of r and r' (Eq. 8) with their n_Gamma and V (Eqs. 10-11),
+    and the pull form of Eq. 15 plus Eq. 16.  Returns a list of [n_Gamma(r), B].
+    """
+    from . import native
+
+    ir = group.irreps[irrep]
+    if ir.rho is None:
+        raise NotImplementedError("irrep is not of real type")
+    N, d = group.n_sites, two_s + 1
+    cache = {}
+
+    def stab_info(label):
+        mask = native.stabilizer(N, d, group.perms, label)
+        key = tuple(int(w) for w in mask)
+        if key not in cache:
+            S = np.array([g for g in range(group.order) if (key[g // 64] >> (g % 64)) & 1])
+            val = float(np.sum(ir.chars[S])) / len(S)
+            nG = int(round(val))
+            P = ir.rho[S].sum(axis=0) / len(S)
+            V, cnt = gram_schmidt_range(P)
+            if cnt != nG:
+                raise ArithmeticError("projector rank differs from the character count")
+            cache[key] = (nG, V, np.sqrt(len(S)))
+        return cache[key]
+
+    out = []
+    for r in rep_labels:
+        r = int(r)
+        n_r, V_r, sq_r = stab_info(r)
+        if n_r == 0:
+            out.append(None)
+            continue
+        rp, gs, cf, diag = native.flip_entries(N, two_s, group.perms, bonds, J, r)
+        x_r = xvals(r, n_r)
+        y = diag * x_r
+        for lab, g_star, c in zip(rp.tolist(), gs.tolist(), cf.tolist()):
+            n_j, V_j, sq_j = stab_info(lab)
+            if n_j == 0:
+                continue
+            g_e = group.inv[g_star]
+            M = V_r.T @ ir.rho[g_e] @ V_j
+            y = y + (c * sq_j / sq_r) * (M[:n_r, :n_j] @ xvals(lab, n_j))
+        out.append(y)
+    return out

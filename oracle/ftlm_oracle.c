@@ -266,3 +266,59 @@ int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Stabilizer bitmask (W words) of one label: bit g set when U(g) n = n (Eq. 8). */
+int or_stab(int N, int d, int G, const int32_t *perms, uint64_t label, uint64_t *mask) {
+    if (N > OR_MAXN) return -1;
+    int a[OR_MAXN];
+    decode(label, N, d, a);
+    const int W = (G + 63) / 64;
+    for (int w = 0; w < W; ++w) mask[w] = 0;
+    for (int g = 0; g < G; ++g)
+        if (image(perms + (size_t)g * N, a, N, d) == label) mask[g / 64] |= 1ull << (g % 64);
+    return 0;
+}
+
+/*
+ * Off-diagonal entries generated by one representative r (Section 2.4): for
+ * every bond and admissible sign, the flipped label's orbit minimum r', the
+ * first minimising element g* (a = U(g*^{-1}) r') and c_a (Eq. 3).  Also the
+ * diagonal energy J sum m_i m_j (Eq. 16).  Returns the entry count (<= cap).
+ */
+int or_flip_entries(int N, int d, int two_s, int G, const int32_t *perms, int n_bonds, const int32_t *bonds,
+                    double J, uint64_t label, int cap, uint64_t *rp, int32_t *gstar, double *coef, double *diag) {
+    if (N > OR_MAXN) return -1;
+    const double s = 0.5 * two_s, ss1 = s * (s + 1.0);
+    int a[OR_MAXN], f[OR_MAXN];
+    decode(label, N, d, a);
+    double dg = 0.0;
+    int cnt = 0;
+    for (int e = 0; e < n_bonds; ++e) {
+        const int si = bonds[2 * e], sj = bonds[2 * e + 1];
+        const double mi = a[si] - s, mj = a[sj] - s;
+        dg += J * mi * mj;
+        for (int sgn = +1; sgn >= -1; sgn -= 2) {
+            const int ai = a[si] + sgn, aj = a[sj] - sgn;
+            if (ai < 0 || ai > two_s || aj < 0 || aj > two_s) continue;
+            if (cnt >= cap) return -2;
+            memcpy(f, a, sizeof(int) * N);
+            f[si] = ai;
+            f[sj] = aj;
+            uint64_t best = UINT64_MAX;
+            int32_t bg = -1;
+            for (int g = 0; g < G; ++g) {
+                uint64_t v = image(perms + (size_t)g * N, f, N, d);
+                if (v < best) {
+                    best = v;
+                    bg = g;
+                }
+            }
+            rp[cnt] = best;
+            gstar[cnt] = bg;
+            coef[cnt] = 0.5 * J * sqrt(ss1 - mi * (mi + sgn)) * sqrt(ss1 - mj * (mj - sgn));
+            ++cnt;
+        }
+    }
+    *diag = dg;
+    return cnt;
+}

@@ -40,6 +40,11 @@ def lib():
         L.or_hv_rows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, P,
                                  ctypes.c_double, ctypes.c_int64, P, P, P, P, P, P, ctypes.c_int, P, ctypes.c_int,
                                  P, P, P, ctypes.c_int64]
+        L.or_stab.restype = ctypes.c_int
+        L.or_stab.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_uint64, P]
+        L.or_flip_entries.restype = ctypes.c_int
+        L.or_flip_entries.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P,
+                                      ctypes.c_double, ctypes.c_uint64, ctypes.c_int, P, P, P, P]
         L.or_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -72,6 +77,30 @@ def min_rep(n_sites, d, perms, label):
     g = np.zeros(1, dtype=np.int32)
     lib().or_min_rep(n_sites, d, perms.shape[0], ptr(perms), int(label), ptr(rep), ptr(g))
     return int(rep[0]), int(g[0])
+
+
+def stabilizer(n_sites, d, perms, label):
+    perms = np.ascontiguousarray(perms, dtype=np.int32)
+    G = perms.shape[0]
+    mask = np.zeros((G + 63) // 64, dtype=np.uint64)
+    lib().or_stab(n_sites, d, G, ptr(perms), int(label), ptr(mask))
+    return mask
+
+
+def flip_entries(n_sites, two_s, perms, bonds, J, label):
+    """(r' labels, g*, c_a, diagonal energy) of every off-diagonal term acting on one representative."""
+    perms = np.ascontiguousarray(perms, dtype=np.int32)
+    bonds = np.ascontiguousarray(bonds, dtype=np.int32)
+    cap = 2 * len(bonds)
+    rp = np.zeros(cap, dtype=np.uint64)
+    gs = np.zeros(cap, dtype=np.int32)
+    cf = np.zeros(cap)
+    dg = np.zeros(1)
+    n = lib().or_flip_entries(n_sites, two_s + 1, two_s, perms.shape[0], ptr(perms), len(bonds), ptr(bonds),
+                              float(J), int(label), cap, ptr(rp), ptr(gs), ptr(cf), ptr(dg))
+    if n < 0:
+        raise RuntimeError("or_flip_entries failed")
+    return rp[:n], gs[:n], cf[:n], float(dg[0])
 
 
 def num_threads() -> int:

@@ -1,0 +1,101 @@
+// Internal structures shared by the translation units of libftlm.
+#pragma once
+
+#include <stdint.h>
+
+#include <array>
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "ftlm.h"
+
+namespace ftlm {
+
+constexpr int kMaxG = 128;      // group order supported on the GPU path (4 elements per lane)
+constexpr int kMaxGHost = 512;  // group order supported by the host group module
+constexpr int kMaxD = 5;        // irrep dimension supported on the GPU path
+constexpr int kMaxBonds = 64;   // bonds per cluster on the GPU path
+constexpr int kMaxB = 32;       // right-hand sides per H·v launch
+
+ftlm_status fail(ftlm_status st, const char *fmt, ...);
+void clear_error();
+void count_launch(int n = 1);
+bool profiling_on();
+
+struct Irrep {
+    int dim = 0;
+    int fs = 1;                 // Frobenius-Schur indicator; 1 = real orthogonal matrices available
+    std::vector<double> chars;  // [G]
+    std::vector<double> rho;    // [G][dim][dim] (empty unless fs == 1)
+};
+
+struct GroupData {
+    int N = 0;
+    int G = 0;
+    std::vector<int32_t> perms;  // [G][N], canonical order, perms[g*N + k] = pi_g(k)
+    std::vector<int32_t> inv;    // [G]
+    std::vector<int32_t> mult;   // [G][G], mult[g*G + h] = index of g h
+    std::vector<int32_t> bonds;  // [n_bonds][2]
+    double J = 1.0;
+    std::vector<Irrep> irreps;
+    int n_bonds() const { return (int)bonds.size() / 2; }
+};
+
+// host group module (group.cpp)
+ftlm_status build_group(int n_sites, int n_gens, const int32_t *gens, int n_bonds, const int32_t *bonds, double J,
+                        GroupData &out);
+ftlm_status compute_irreps(GroupData &g);
+ftlm_status canonicalise_and_verify_irreps(GroupData &g, std::vector<Irrep> &irreps, double tol);
+
+}  // namespace ftlm
+
+struct ftlm_group {
+    ftlm::GroupData d;
+};
+
+// Packed-label sector on the device (basis.cu).
+struct ftlm_sector {
+    std::atomic<int> refs{1};
+    ftlm::GroupData grp;
+    int two_s = 0, two_M = 0, bits = 0, N = 0, G = 0, A = 0;
+    bool half = false;  // s = 1/2 with N <= 32: 32-bit labels, XOR flips
+    uint64_t n_reps = 0, sector_dim = 0;
+    uint64_t *d_labels = nullptr;   // [n_reps] ascending packed labels
+    uint16_t *d_stab_id = nullptr;  // [n_reps] stabilizer subgroup id (0 = trivial)
+    std::vector<std::array<uint64_t, 2>> stab_masks;  // per id
+    std::vector<std::vector<int>> stab_elems;         // per id
+    uint32_t *d_bucket = nullptr;                     // [n_buckets + 1] first rep index of each bucket
+    int bucket_shift = 0;
+    uint64_t n_buckets = 0;
+    // H·v search tables
+    uint32_t *d_lut = nullptr;   // s = 1/2: [nchunk][16][kMaxG] image of a 4-site nibble under g
+    int n_chunks = 0;
+    uint8_t *d_pos = nullptr;    // general s: [kMaxG][64] bit position of site k's field after g
+    void *d_dtab = nullptr;      // [n_bonds][kMaxG] u32 XOR masks (s = 1/2) or int64 deltas (general)
+    uint8_t *d_bonds = nullptr;  // [n_bonds][2] site pairs
+    int *d_err = nullptr;        // device error word
+    size_t device_bytes = 0;
+};
+
+struct ftlm_basis {
+    ftlm_sector *sec = nullptr;
+    int irrep = 0, d = 0;
+    uint64_t dim = 0;
+    uint64_t *d_off = nullptr;      // [n_reps + 1]
+    // per stabilizer id: n_Gamma, sqrt|Stab|, V [d][d] (V[beta*d + k])
+    uint8_t *d_ntab = nullptr;
+    double *d_sqrtS = nullptr;
+    float *d_sqrtSf = nullptr;
+    double *d_V = nullptr;
+    float *d_Vf = nullptr;
+    // rho(g)^T per element, [G][d][d]: rhoT[g][b][c] = rho(g)[c][b]
+    double *d_rhoT = nullptr;
+    float *d_rhoTf = nullptr;
+    std::vector<uint8_t> h_ntab;
+    size_t device_bytes = 0;
+};
+
+namespace ftlm {
+void sector_release(ftlm_sector *s);
+}

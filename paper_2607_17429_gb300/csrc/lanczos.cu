@@ -1,0 +1,582 @@
+// FTLM on the GPU (Section 2.2 of arXiv 2607.17429): start vectors, the
+// three-term Lanczos recurrence with FP64 dot products and norms, the FP64
+// tridiagonal eigensolve, and the thermal sums of Eqs. 5-7 with Eq. 14 weights.
+//
+// Reductions are deterministic: a fixed grid, a fixed row partition per block
+// and a fixed summation order, so repeated runs give identical coefficients.
+#include <float.h>
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace ftlm {
+
+ftlm_status hv_launch_f64(const ftlm_basis *bs, int B, const double *x, double *y, cudaStream_t stream);
+ftlm_status hv_launch_f32(const ftlm_basis *bs, int B, const float *x, float *y, cudaStream_t stream);
+
+namespace {
+
+constexpr int kRedBlocks = kNumSMs * 4;  // fixed reduction grid (deterministic order)
+constexpr int kRedThreads = 256;
+
+// ---------------------------------------------------------------- Philox4x32-10 (Salmon et al., SC'11)
+
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    }
+    return c;
+}
+
+__device__ __forceinline__ double start_value(uint64_t row, uint32_t chain, uint32_t k0, uint32_t k1, int rng) {
+    const U4 o = philox4x32_10(U4{(uint32_t)row, (uint32_t)(row >> 32), chain, 0u}, k0, k1);
+    if (rng == FTLM_RADEMACHER) return (o.x & 1u) ? -1.0 : 1.0;
+    const double u1 = ((double)(((uint64_t)(o.x >> 5) << 26) | (o.y >> 6)) + 0.5) * 0x1p-53;
+    const double u2 = (double)(((uint64_t)(o.z >> 5) << 26) | (o.w >> 6)) * 0x1p-53;
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+// Threads of a reduction block are (row lane r, column b): t = r * B + b.
+__device__ __forceinline__ int red_rows(int B) { return kRedThreads / B; }
+
+__device__ void block_partial(double acc, int B, double *partials) {
+    __shared__ double s[kRedThreads];
+    const int nr = red_rows(B);
+    const int t = threadIdx.x;
+    s[t] = (t < nr * B) ? acc : 0.0;
+    __syncthreads();
+    if (t < B) {
+        double sum = 0.0;
+        for (int r = 0; r < nr; ++r) sum += s[r * B + t];
+        partials[(size_t)blockIdx.x * B + t] = sum;
+    }
+}
+
+template <typename VT>
+__global__ void lz_random(VT *v, uint64_t dim, int B, int Bc, uint32_t chain0, uint32_t k0, uint32_t k1, int rng,
+                          double *partials) {
+    const int nr = red_rows(B);
+    const int r = threadIdx.x / B, b = threadIdx.x % B;
+    double acc = 0.0;
+    if (r < nr) {
+        for (uint64_t i = (uint64_t)blockIdx.x * nr + r; i < dim; i += (uint64_t)gridDim.x * nr) {
+            double val = b < Bc ? start_value(i, chain0 + b, k0, k1, rng) : 0.0;
+            const VT st = (VT)val;
+            v[i * B + b] = st;
+            acc += (double)st * (double)st;
+        }
+    }
+    block_partial(acc, B, partials);
+}
+
+template <typename VT>
+__global__ void lz_dot(const VT *v, const VT *w, uint64_t dim, int B, double *partials) {
+    const int nr = red_rows(B);
+    const int r = threadIdx.x / B, b = threadIdx.x % B;
+    double acc = 0.0;
+    if (r < nr)
+        for (uint64_t i = (uint64_t)blockIdx.x * nr + r; i < dim; i += (uint64_t)gridDim.x * nr)
+            acc += (double)v[i * B + b] * (double)w[i * B + b];
+    block_partial(acc, B, partials);
+}
+
+struct LzState {
+    double *alpha;      // [n_steps][B]
+    double *beta;       // [n_steps][B]
+    double *beta_prev;  // [B]
+    double *scale;      // [B] 1/norm of the vector being normalised
+    int *active;        // [B]
+    int *steps;         // [B]
+};
+
+// w -= alpha v + beta_prev v_prev, partial |w|^2
+template <typename VT>
+__global__ void lz_update(VT *w, const VT *v, const VT *vp, uint64_t dim, int B, int j, LzState st, double *partials) {
+    const int nr = red_rows(B);
+    const int r = threadIdx.x / B, b = threadIdx.x % B;
+    double acc = 0.0;
+    if (r < nr) {
+        const double al = st.alpha[(size_t)j * B + b], bp = st.beta_prev[b];
+        for (uint64_t i = (uint64_t)blockIdx.x * nr + r; i < dim; i += (uint64_t)gridDim.x * nr) {
+            const size_t e = i * B + b;
+            const VT nw = (VT)((double)w[e] - al * (double)v[e] - bp * (double)vp[e]);
+            w[e] = nw;
+            acc += (double)nw * (double)nw;
+        }
+    }
+    block_partial(acc, B, partials);
+}
+
+template <typename VT>
+__global__ void lz_scale(VT *w, uint64_t dim, int B, LzState st) {
+    const uint64_t n = dim * (uint64_t)B;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (uint64_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e % B);
+        w[e] = st.active[b] ? (VT)((double)w[e] * st.scale[b]) : (VT)0;
+    }
+}
+
+__device__ double sum_partials(const double *p, int B, int b) {
+    double s = 0.0;
+    for (int k = 0; k < kRedBlocks; ++k) s += p[(size_t)k * B + b];
+    return s;
+}
+
+__global__ void fin_norm(const double *p, int B, LzState st) {
+    const int b = threadIdx.x;
+    if (b >= B) return;
+    const double n = sqrt(sum_partials(p, B, b));
+    st.scale[b] = n > 0 ? 1.0 / n : 0.0;
+    st.active[b] = n > 0;
+    st.steps[b] = 0;
+    st.beta_prev[b] = 0.0;
+}
+
+__global__ void fin_alpha(const double *p, int B, int j, LzState st) {
+    const int b = threadIdx.x;
+    if (b >= B) return;
+    st.alpha[(size_t)j * B + b] = st.active[b] ? sum_partials(p, B, b) : 0.0;
+}
+
+__global__ void fin_beta(const double *p, int B, int j, int m_max, double tol, LzState st) {
+    const int b = threadIdx.x;
+    if (b >= B) return;
+    if (!st.active[b]) {
+        st.beta[(size_t)j * B + b] = 0.0;
+        return;
+    }
+    const double bn = sqrt(sum_partials(p, B, b));
+    const double al = st.alpha[(size_t)j * B + b];
+    st.beta[(size_t)j * B + b] = bn;
+    if (j + 1 >= m_max || bn <= tol * (fabs(al) + st.beta_prev[b])) {
+        st.active[b] = 0;
+        st.steps[b] = j + 1;
+    } else {
+        st.beta_prev[b] = bn;
+        st.scale[b] = 1.0 / bn;
+    }
+}
+
+// ---------------------------------------------------------------- tridiagonal eigensolve (implicit QL, FP64)
+
+// Eigenvalues of the symmetric tridiagonal matrix (diag d[0..n-1], off-diagonal
+// e[i] between i and i+1) and the first row z of its orthonormal eigenvector
+// matrix.  Implicit QL sweeps with the shift taken from the leading 2x2 block;
+// each Givens rotation is also applied to z.  Returns false if a block does not
+// converge within 60 sweeps.
+__device__ bool tridiag_ql(int n, double *d, double *e, double *z) {
+    for (int i = 0; i < n; ++i) z[i] = (i == 0) ? 1.0 : 0.0;
+    if (n > 0) e[n - 1] = 0.0;
+    for (int l = 0; l < n; ++l) {
+        for (int sweep = 0;; ++sweep) {
+            int m = l;
+            for (; m < n - 1; ++m) {
+                const double dd = fabs(d[m]) + fabs(d[m + 1]);
+                if (fabs(e[m]) <= DBL_EPSILON * dd) break;
+            }
+            if (m == l) break;
+            if (sweep == 60) return false;
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+            double s = 1.0, c = 1.0, p = 0.0;
+            bool deflated = false;
+            for (int i = m - 1; i >= l; --i) {
+                const double f = s * e[i], bb = c * e[i];
+                r = hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) {
+                    d[i + 1] -= p;
+                    e[m] = 0.0;
+                    deflated = true;
+                    break;
+                }
+                s = f / r;
+                c = g / r;
+                g = d[i + 1] - p;
+                r = (d[i] - g) * s + 2.0 * c * bb;
+                p = s * r;
+                d[i + 1] = g + p;
+                g = c * r - bb;
+                const double zi = z[i], zi1 = z[i + 1];
+                z[i + 1] = s * zi + c * zi1;
+                z[i] = c * zi - s * zi1;
+            }
+            if (deflated) continue;
+            d[l] -= p;
+            e[l] = g;
+            e[m] = 0.0;
+        }
+    }
+    return true;
+}
+
+constexpr int kMaxSteps = 512;
+
+// one thread per chain: theta, w (sorted ascending) from alpha/beta rows of length m[c]
+__global__ void ritz_kernel(int n_chains, int ld, const int *m, const double *alpha, const double *beta, double *theta,
+                            double *w, int *err) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_chains) return;
+    const int n = m[c];
+    double *d = theta + (size_t)c * ld, *z = w + (size_t)c * ld;
+    double e[kMaxSteps];
+    for (int i = 0; i < ld; ++i) {
+        d[i] = 0.0;
+        z[i] = 0.0;
+    }
+    if (n <= 0) return;
+    if (n > kMaxSteps) {
+        atomicOr(err, 2);
+        return;
+    }
+    for (int i = 0; i < n; ++i) {
+        d[i] = alpha[(size_t)c * ld + i];
+        e[i] = beta[(size_t)c * ld + i];
+    }
+    if (!tridiag_ql(n, d, e, z)) atomicOr(err, 1);
+    for (int i = 0; i < n; ++i) z[i] *= z[i];
+    for (int i = 1; i < n; ++i) {  // insertion sort by theta
+        const double td = d[i], tz = z[i];
+        int k = i - 1;
+        while (k >= 0 && d[k] > td) {
+            d[k + 1] = d[k];
+            z[k + 1] = z[k];
+            --k;
+        }
+        d[k + 1] = td;
+        z[k + 1] = tz;
+    }
+}
+
+// ---------------------------------------------------------------- thermal sums (Eqs. 5-7, 14)
+
+struct ThermoIn {
+    int n_chains, ld;
+    const int *m;
+    const double *theta, *w, *Wc, *Msq;
+};
+
+__device__ double block_sum(double v) {
+    __shared__ double s[kRedThreads];
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double r = s[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ double block_min(double v) {
+    __shared__ double s[kRedThreads];
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) s[threadIdx.x] = fmin(s[threadIdx.x], s[threadIdx.x + o]);
+        __syncthreads();
+    }
+    const double r = s[0];
+    __syncthreads();
+    return r;
+}
+
+__global__ void ground_energy(ThermoIn in, double *E0) {
+    double mn = INFINITY;
+    const uint64_t n = (uint64_t)in.n_chains * in.ld;
+    for (uint64_t t = threadIdx.x; t < n; t += blockDim.x) {
+        const int c = (int)(t / in.ld), k = (int)(t % in.ld);
+        if (k < in.m[c]) mn = fmin(mn, in.theta[t]);
+    }
+    mn = block_min(mn);
+    if (threadIdx.x == 0) *E0 = mn;
+}
+
+__global__ void thermo_kernel(ThermoIn in, const double *T, const double *E0p, double g, double *out /*[4][n_T]*/,
+                              int n_T) {
+    const int it = blockIdx.x;
+    const double beta = 1.0 / T[it], E0 = *E0p;
+    const uint64_t n = (uint64_t)in.n_chains * in.ld;
+    double z = 0.0, ze = 0.0, zm = 0.0;
+    for (uint64_t t = threadIdx.x; t < n; t += blockDim.x) {
+        const int c = (int)(t / in.ld), k = (int)(t % in.ld);
+        if (k >= in.m[c]) continue;
+        const double bz = in.Wc[c] * in.w[t] * exp(-beta * (in.theta[t] - E0));
+        z += bz;
+        ze += bz * in.theta[t];
+        zm += bz * in.Msq[c];
+    }
+    z = block_sum(z);
+    ze = block_sum(ze);
+    zm = block_sum(zm);
+    const double Em = ze / z;
+    double v = 0.0;
+    for (uint64_t t = threadIdx.x; t < n; t += blockDim.x) {
+        const int c = (int)(t / in.ld), k = (int)(t % in.ld);
+        if (k >= in.m[c]) continue;
+        const double bz = in.Wc[c] * in.w[t] * exp(-beta * (in.theta[t] - E0));
+        const double dt = in.theta[t] - Em;
+        v += bz * dt * dt;
+    }
+    v = block_sum(v);
+    if (threadIdx.x == 0) {
+        out[it] = log(z) - beta * E0;
+        out[n_T + it] = Em;
+        out[2 * n_T + it] = beta * beta * v / z;
+        out[3 * n_T + it] = g * g * beta * zm / z;
+    }
+}
+
+template <typename VT>
+ftlm_status hv_any(const ftlm_basis *b, int B, const VT *x, VT *y, cudaStream_t st);
+template <>
+ftlm_status hv_any<double>(const ftlm_basis *b, int B, const double *x, double *y, cudaStream_t st) {
+    return hv_launch_f64(b, B, x, y, st);
+}
+template <>
+ftlm_status hv_any<float>(const ftlm_basis *b, int B, const float *x, float *y, cudaStream_t st) {
+    return hv_launch_f32(b, B, x, y, st);
+}
+
+template <typename VT>
+ftlm_status lanczos_impl(const ftlm_basis *bs, int R, int n_steps, uint64_t seed, uint64_t block_id, int rng,
+                         cudaStream_t stream, double *alpha, double *beta, int *steps_done) {
+    const uint64_t dim = bs->dim;
+    const int Bmax = std::min(R, kMaxB);
+    const int m_max = (int)std::min<uint64_t>((uint64_t)n_steps, dim);
+    const double tol = sizeof(VT) == 8 ? 1e-12 : 1e-6;
+    for (int r = 0; r < R; ++r) {
+        steps_done[r] = 0;
+        for (int j = 0; j < n_steps; ++j) alpha[(size_t)r * n_steps + j] = beta[(size_t)r * n_steps + j] = 0.0;
+    }
+    if (dim == 0 || m_max == 0) return FTLM_OK;
+    DevBuf<VT> v0, v1, v2;
+    FTLM_CUDA(v0.alloc(dim * Bmax));
+    FTLM_CUDA(v1.alloc(dim * Bmax));
+    FTLM_CUDA(v2.alloc(dim * Bmax));
+    DevBuf<double> partials, dstate;
+    DevBuf<int> istate;
+    FTLM_CUDA(partials.alloc((size_t)kRedBlocks * Bmax));
+    FTLM_CUDA(dstate.alloc((size_t)2 * m_max * Bmax + 2 * Bmax));
+    FTLM_CUDA(istate.alloc((size_t)2 * Bmax));
+    LzState st;
+    st.alpha = dstate.p;
+    st.beta = dstate.p + (size_t)m_max * Bmax;
+    st.beta_prev = dstate.p + (size_t)2 * m_max * Bmax;
+    st.scale = st.beta_prev + Bmax;
+    st.active = istate.p;
+    st.steps = istate.p + Bmax;
+    std::vector<double> ha((size_t)m_max * Bmax), hb((size_t)m_max * Bmax);
+    std::vector<int> hs(Bmax);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)block_id;
+    const int scale_blocks = kNumSMs * 8;
+    for (int chain0 = 0; chain0 < R; chain0 += Bmax) {
+        const int Bc = std::min(Bmax, R - chain0);
+        const int B = Bc;  // vectors are [dim][Bc]
+        VT *vp = v0.p, *v = v1.p, *w = v2.p;
+        FTLM_CUDA(cudaMemsetAsync(dstate.p, 0, ((size_t)2 * m_max * Bmax + 2 * Bmax) * sizeof(double), stream));
+        FTLM_CUDA(cudaMemsetAsync(vp, 0, dim * B * sizeof(VT), stream));
+        count_launch();
+        lz_random<VT><<<kRedBlocks, kRedThreads, 0, stream>>>(v, dim, B, Bc, (uint32_t)chain0, k0, k1, rng,
+                                                              partials.p);
+        count_launch();
+        fin_norm<<<1, 32, 0, stream>>>(partials.p, B, st);
+        count_launch();
+        lz_scale<VT><<<scale_blocks, 256, 0, stream>>>(v, dim, B, st);
+        FTLM_CUDA(cudaGetLastError());
+        for (int j = 0; j < m_max; ++j) {
+            ftlm_status s = hv_any<VT>(bs, B, v, w, stream);
+            if (s != FTLM_OK) return s;
+            count_launch();
+            lz_dot<VT><<<kRedBlocks, kRedThreads, 0, stream>>>(v, w, dim, B, partials.p);
+            count_launch();
+            fin_alpha<<<1, 32, 0, stream>>>(partials.p, B, j, st);
+            count_launch();
+            lz_update<VT><<<kRedBlocks, kRedThreads, 0, stream>>>(w, v, vp, dim, B, j, st, partials.p);
+            count_launch();
+            fin_beta<<<1, 32, 0, stream>>>(partials.p, B, j, m_max, tol, st);
+            count_launch();
+            lz_scale<VT><<<scale_blocks, 256, 0, stream>>>(w, dim, B, st);
+            FTLM_CUDA(cudaGetLastError());
+            VT *t = vp;
+            vp = v;
+            v = w;
+            w = t;
+        }
+        FTLM_CUDA(cudaMemcpyAsync(ha.data(), st.alpha, (size_t)m_max * B * 8, cudaMemcpyDeviceToHost, stream));
+        FTLM_CUDA(cudaMemcpyAsync(hb.data(), st.beta, (size_t)m_max * B * 8, cudaMemcpyDeviceToHost, stream));
+        FTLM_CUDA(cudaMemcpyAsync(hs.data(), st.steps, (size_t)B * 4, cudaMemcpyDeviceToHost, stream));
+        FTLM_CUDA(cudaStreamSynchronize(stream));
+        int err = 0;
+        FTLM_CUDA(cudaMemcpy(&err, bs->sec->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) return fail(FTLM_EINTERNAL, "device bounds check tripped in H·v (code %d)", err);
+        for (int b = 0; b < Bc; ++b) {
+            const int r = chain0 + b;
+            steps_done[r] = hs[b];
+            for (int j = 0; j < hs[b]; ++j) {
+                alpha[(size_t)r * n_steps + j] = ha[(size_t)j * B + b];
+                beta[(size_t)r * n_steps + j] = hb[(size_t)j * B + b];
+            }
+        }
+    }
+    return FTLM_OK;
+}
+
+}  // namespace
+}  // namespace ftlm
+
+using namespace ftlm;
+
+extern "C" {
+
+ftlm_status ftlm_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y, void *cuda_stream) {
+    if (!b || !x || !y) return fail(FTLM_EINVAL, "NULL argument");
+    if (B < 1 || B > kMaxB) return fail(FTLM_EINVAL, "B must be in 1..%d", kMaxB);
+    if (b->dim == 0) return FTLM_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (dtype == FTLM_F64) return hv_launch_f64(b, B, (const double *)x, (double *)y, st);
+    if (dtype == FTLM_F32) return hv_launch_f32(b, B, (const float *)x, (float *)y, st);
+    return fail(FTLM_EINVAL, "unknown dtype");
+}
+
+ftlm_status ftlm_lanczos(const ftlm_basis *b, ftlm_dtype dtype, int R, int n_steps, uint64_t seed, uint64_t block_id,
+                         ftlm_rng rng, void *cuda_stream, double *alpha, double *beta, int *steps_done) {
+    if (!b || !alpha || !beta || !steps_done) return fail(FTLM_EINVAL, "NULL argument");
+    if (R < 1 || n_steps < 1 || n_steps > kMaxSteps) return fail(FTLM_EINVAL, "R >= 1 and 1 <= n_steps <= 512");
+    if (rng != FTLM_GAUSS && rng != FTLM_RADEMACHER) return fail(FTLM_EINVAL, "unknown rng");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (dtype == FTLM_F64) return lanczos_impl<double>(b, R, n_steps, seed, block_id, rng, st, alpha, beta, steps_done);
+    if (dtype == FTLM_F32) return lanczos_impl<float>(b, R, n_steps, seed, block_id, rng, st, alpha, beta, steps_done);
+    return fail(FTLM_EINVAL, "unknown dtype");
+}
+
+ftlm_status ftlm_ritz(int n_chains, int ld, const int *m, const double *alpha, const double *beta, double *theta,
+                      double *w, void *cuda_stream) {
+    if (n_chains < 0 || ld < 1 || ld > kMaxSteps || !m || !alpha || !beta || !theta || !w)
+        return fail(FTLM_EINVAL, "bad arguments");
+    if (n_chains == 0) return FTLM_OK;
+    for (int c = 0; c < n_chains; ++c)
+        if (m[c] < 0 || m[c] > ld) return fail(FTLM_EINVAL, "steps out of range");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t n = (size_t)n_chains * ld;
+    DevBuf<double> da, db, dt, dw;
+    DevBuf<int> dm, derr;
+    FTLM_CUDA(da.alloc(n));
+    FTLM_CUDA(db.alloc(n));
+    FTLM_CUDA(dt.alloc(n));
+    FTLM_CUDA(dw.alloc(n));
+    FTLM_CUDA(dm.alloc(n_chains));
+    FTLM_CUDA(derr.alloc(1));
+    FTLM_CUDA(cudaMemcpyAsync(da.p, alpha, n * 8, cudaMemcpyHostToDevice, st));
+    FTLM_CUDA(cudaMemcpyAsync(db.p, beta, n * 8, cudaMemcpyHostToDevice, st));
+    FTLM_CUDA(cudaMemcpyAsync(dm.p, m, n_chains * 4, cudaMemcpyHostToDevice, st));
+    FTLM_CUDA(cudaMemsetAsync(derr.p, 0, 4, st));
+    count_launch();
+    ritz_kernel<<<(n_chains + 63) / 64, 64, 0, st>>>(n_chains, ld, dm.p, da.p, db.p, dt.p, dw.p, derr.p);
+    FTLM_CUDA(cudaGetLastError());
+    int err = 0;
+    FTLM_CUDA(cudaMemcpyAsync(theta, dt.p, n * 8, cudaMemcpyDeviceToHost, st));
+    FTLM_CUDA(cudaMemcpyAsync(w, dw.p, n * 8, cudaMemcpyDeviceToHost, st));
+    FTLM_CUDA(cudaMemcpyAsync(&err, derr.p, 4, cudaMemcpyDeviceToHost, st));
+    FTLM_CUDA(cudaStreamSynchronize(st));
+    if (err) return fail(FTLM_EINTERNAL, "tridiagonal eigensolve did not converge");
+    return FTLM_OK;
+}
+
+ftlm_status ftlm_thermo(int n_blocks, const ftlm_block *blocks, int n_T, const double *T, double g, double *lnZ,
+                        double *E, double *C, double *chi, double *E0, void *cuda_stream) {
+    if (n_blocks < 1 || !blocks || n_T < 1 || !T) return fail(FTLM_EINVAL, "bad arguments");
+    for (int t = 0; t < n_T; ++t)
+        if (!(T[t] > 0)) return fail(FTLM_EINVAL, "temperatures must be positive");
+    int ld = 1, n_chains = 0;
+    for (int k = 0; k < n_blocks; ++k) {
+        const ftlm_block &bl = blocks[k];
+        if (bl.R < 1 || bl.ld < 1 || !bl.steps_done || !bl.alpha || !bl.beta) return fail(FTLM_EINVAL, "bad block");
+        for (int r = 0; r < bl.R; ++r) {
+            if (bl.steps_done[r] < 0 || bl.steps_done[r] > bl.ld) return fail(FTLM_EINVAL, "steps out of range");
+            ld = std::max(ld, bl.steps_done[r]);
+        }
+        n_chains += bl.R;
+    }
+    if (ld > kMaxSteps) return fail(FTLM_EINVAL, "too many steps");
+    std::vector<double> a((size_t)n_chains * ld, 0.0), b((size_t)n_chains * ld, 0.0), Wc(n_chains), Msq(n_chains);
+    std::vector<int> m(n_chains);
+    int c = 0;
+    for (int k = 0; k < n_blocks; ++k) {
+        const ftlm_block &bl = blocks[k];
+        const double mult = bl.two_M > 0 ? 2.0 : 1.0;
+        for (int r = 0; r < bl.R; ++r, ++c) {
+            m[c] = bl.steps_done[r];
+            for (int j = 0; j < m[c]; ++j) {
+                a[(size_t)c * ld + j] = bl.alpha[(size_t)r * bl.ld + j];
+                b[(size_t)c * ld + j] = bl.beta[(size_t)r * bl.ld + j];
+            }
+            Wc[c] = mult * bl.d_gamma * (double)bl.dim / bl.R;
+            Msq[c] = 0.25 * bl.two_M * bl.two_M;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t n = (size_t)n_chains * ld;
+    DevBuf<double> da, db, dt, dw, dW, dM, dT, dE0, dout;
+    DevBuf<int> dm, derr;
+    FTLM_CUDA(da.alloc(n));
+    FTLM_CUDA(db.alloc(n));
+    FTLM_CUDA(dt.alloc(n));
+    FTLM_CUDA(dw.alloc(n));
+    FTLM_CUDA(dW.alloc(n_chains));
+    FTLM_CUDA(dM.alloc(n_chains));
+    FTLM_CUDA(dT.alloc(n_T));
+    FTLM_CUDA(dE0.alloc(1));
+    FTLM_CUDA(dout.alloc((size_t)4 * n_T));
+    FTLM_CUDA(dm.alloc(n_chains));
+    FTLM_CUDA(derr.alloc(1));
+    FTLM_CUDA(cudaMemcpyAsync(da.p, a.data(), n * 8, cudaMemcpyHostToDevice, st));
+    FTLM_CUDA(cudaMemcpyAsync(db.p, b.data(), n * 8, cudaMemcpyHostToDevice, st));
+    FTLM_CUDA(cudaMemcpyAsync(dW.p, Wc.data(), n_chains * 8, cudaMemcpyHostToDevice, st));
+    FTLM_CUDA(cudaMemcpyAsync(dM.p, Msq.data(), n_chains * 8, cudaMemcpyHostToDevice, st));
+    FTLM_CUDA(cudaMemcpyAsync(dm.p, m.data(), n_chains * 4, cudaMemcpyHostToDevice, st));
+    FTLM_CUDA(cudaMemcpyAsync(dT.p, T, n_T * 8, cudaMemcpyHostToDevice, st));
+    FTLM_CUDA(cudaMemsetAsync(derr.p, 0, 4, st));
+    count_launch();
+    ritz_kernel<<<(n_chains + 63) / 64, 64, 0, st>>>(n_chains, ld, dm.p, da.p, db.p, dt.p, dw.p, derr.p);
+    ThermoIn in{n_chains, ld, dm.p, dt.p, dw.p, dW.p, dM.p};
+    count_launch();
+    ground_energy<<<1, kRedThreads, 0, st>>>(in, dE0.p);
+    count_launch();
+    thermo_kernel<<<n_T, kRedThreads, 0, st>>>(in, dT.p, dE0.p, g, dout.p, n_T);
+    FTLM_CUDA(cudaGetLastError());
+    std::vector<double> out((size_t)4 * n_T);
+    double e0 = 0.0;
+    int err = 0;
+    FTLM_CUDA(cudaMemcpyAsync(out.data(), dout.p, out.size() * 8, cudaMemcpyDeviceToHost, st));
+    FTLM_CUDA(cudaMemcpyAsync(&e0, dE0.p, 8, cudaMemcpyDeviceToHost, st));
+    FTLM_CUDA(cudaMemcpyAsync(&err, derr.p, 4, cudaMemcpyDeviceToHost, st));
+    FTLM_CUDA(cudaStreamSynchronize(st));
+    if (err) return fail(FTLM_EINTERNAL, "tridiagonal eigensolve did not converge");
+    for (int t = 0; t < n_T; ++t) {
+        if (lnZ) lnZ[t] = out[t];
+        if (E) E[t] = out[n_T + t];
+        if (C) C[t] = out[2 * n_T + t];
+        if (chi) chi[t] = out[3 * n_T + t];
+    }
+    if (E0) *E0 = e0;
+    return FTLM_OK;
+}
+
+}  // extern "C"

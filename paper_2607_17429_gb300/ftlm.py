@@ -1,0 +1,326 @@
+"""Thin ctypes binding of libftlm.so (the C ABI in include/ftlm.h).
+
+Functions keep the C names; this module only marshals arguments (numpy arrays
+for host buffers, integer device pointers / torch tensors for device buffers)
+and turns a non-zero ftlm_status into ``FtlmError``.  Every step of the
+computation runs in the library.  Importing fails loudly when the library has
+not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOTGROUP, EBONDS, EIRREP, EUNSUPPORTED, ENOMEM, ECUDA, ETIMEOUT, EINTERNAL = range(10)
+F64, F32 = 0, 1
+GAUSS, RADEMACHER = 0, 1
+
+LIB_PATH = _build.LIB
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libftlm.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                      f"python -m paper_2607_17429_gb300.build")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_U64 = ctypes.c_uint64
+
+
+class FtlmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"ftlm status {status}: {msg}")
+        self.status = status
+
+
+class ftlm_profile(ctypes.Structure):
+    _fields_ = [("kernel_launches", _U64), ("hv_launches", _U64), ("hv_ms", ctypes.c_double), ("hv_rows", _U64)]
+
+
+class ftlm_block(ctypes.Structure):
+    _fields_ = [("two_M", _I), ("d_gamma", _I), ("dim", _U64), ("R", _I), ("ld", _I),
+                ("steps_done", _P), ("alpha", _P), ("beta", _P)]
+
+
+_SIGS = {
+    "ftlm_group_init": [_I, _I, _P, _I, _P, ctypes.c_double, _P],
+    "ftlm_group_builtin": [ctypes.c_char_p, _P],
+    "ftlm_group_info": [_P, _P, _P, _P, _P, _P, _P],
+    "ftlm_group_irrep": [_P, _I, _P, _P],
+    "ftlm_group_bonds": [_P, _P, _P, _P],
+    "ftlm_group_set_irreps": [_P, _I, _P, _P],
+    "ftlm_build_sector": [_P, _I, _I, _P, _P],
+    "ftlm_sector_info": [_P, _P, _P, _P],
+    "ftlm_sector_export": [_P, _P, _P],
+    "ftlm_build_block": [_P, _I, _P, _P],
+    "ftlm_build_basis": [_P, _I, _I, _I, _P, _P],
+    "ftlm_basis_info": [_P, _P, _P, _P],
+    "ftlm_basis_export": [_P, _P, _P, _P, _P],
+    "ftlm_basis_check": [_P, _P],
+    "ftlm_hv": [_P, _I, _I, _P, _P, _P],
+    "ftlm_lanczos": [_P, _I, _I, _I, _U64, _U64, _I, _P, _P, _P, _P],
+    "ftlm_ritz": [_I, _I, _P, _P, _P, _P, _P, _P],
+    "ftlm_thermo": [_I, _P, _I, _P, ctypes.c_double, _P, _P, _P, _P, _P, _P],
+    "ftlm_profile_enable": [_I],
+    "ftlm_profile_reset": [],
+    "ftlm_profile_get": [_P],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+for _name in ("ftlm_group_free", "ftlm_sector_free", "ftlm_basis_free"):
+    getattr(_lib, _name).argtypes = [_P]
+    getattr(_lib, _name).restype = None
+_lib.ftlm_last_error.restype = ctypes.c_char_p
+_lib.ftlm_last_error.argtypes = []
+
+EXPORTED = sorted(list(_SIGS) + ["ftlm_group_free", "ftlm_sector_free", "ftlm_basis_free", "ftlm_last_error"])
+
+
+def _check(st):
+    if st != OK:
+        raise FtlmError(st, _lib.ftlm_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):  # torch tensor
+        return a.data_ptr()
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+def ftlm_last_error() -> str:
+    return _lib.ftlm_last_error().decode()
+
+
+# ---------------------------------------------------------------- group
+
+
+class Group:
+    """Owning handle of an ftlm_group."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.ftlm_group_free(self._h)
+            self._h = None
+
+
+def ftlm_group_init(gens, bonds, J=1.0) -> Group:
+    gens = np.ascontiguousarray(gens, dtype=np.int32)
+    bonds = np.ascontiguousarray(bonds, dtype=np.int32).reshape(-1, 2)
+    h = ctypes.c_void_p()
+    _check(_lib.ftlm_group_init(gens.shape[1], gens.shape[0], _ptr(gens), bonds.shape[0], _ptr(bonds), float(J),
+                                ctypes.byref(h)))
+    return Group(h.value)
+
+
+def ftlm_group_builtin(name: str) -> Group:
+    h = ctypes.c_void_p()
+    _check(_lib.ftlm_group_builtin(name.encode(), ctypes.byref(h)))
+    return Group(h.value)
+
+
+def ftlm_group_info(g: Group) -> dict:
+    n_sites, order, n_irreps = _I(), _I(), _I()
+    _check(_lib.ftlm_group_info(g.handle, ctypes.byref(n_sites), ctypes.byref(order), ctypes.byref(n_irreps),
+                                None, None, None))
+    dims = np.zeros(n_irreps.value, dtype=np.int32)
+    fs = np.zeros(n_irreps.value, dtype=np.int32)
+    chars = np.zeros((n_irreps.value, order.value))
+    _check(_lib.ftlm_group_info(g.handle, None, None, None, _ptr(dims), _ptr(fs), _ptr(chars)))
+    return dict(n_sites=n_sites.value, order=order.value, dims=dims, fs=fs, chars=chars)
+
+
+def ftlm_group_irrep(g: Group, irrep: int | None = None):
+    info = ftlm_group_info(g)
+    perms = np.zeros((info["order"], info["n_sites"]), dtype=np.int32)
+    rho = None
+    if irrep is not None:
+        d = int(info["dims"][irrep])
+        rho = np.zeros((info["order"], d, d))
+    _check(_lib.ftlm_group_irrep(g.handle, -1 if irrep is None else int(irrep), _ptr(rho), _ptr(perms)))
+    return rho, perms
+
+
+def ftlm_group_bonds(g: Group):
+    nb, J = _I(), ctypes.c_double()
+    _check(_lib.ftlm_group_bonds(g.handle, ctypes.byref(nb), None, ctypes.byref(J)))
+    bonds = np.zeros((nb.value, 2), dtype=np.int32)
+    _check(_lib.ftlm_group_bonds(g.handle, None, _ptr(bonds), None))
+    return bonds, J.value
+
+
+def ftlm_group_set_irreps(g: Group, rhos) -> None:
+    dims = np.array([r.shape[1] for r in rhos], dtype=np.int32)
+    flat = np.ascontiguousarray(np.concatenate([np.ascontiguousarray(r, dtype=np.float64).ravel() for r in rhos]))
+    _check(_lib.ftlm_group_set_irreps(g.handle, len(rhos), _ptr(dims), _ptr(flat)))
+
+
+# ---------------------------------------------------------------- sector / block
+
+
+class Sector:
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.ftlm_sector_free(self._h)
+            self._h = None
+
+
+class Basis:
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.ftlm_basis_free(self._h)
+            self._h = None
+
+
+def ftlm_build_sector(g: Group, two_s: int, two_M: int, stream=None) -> Sector:
+    h = ctypes.c_void_p()
+    _check(_lib.ftlm_build_sector(g.handle, two_s, two_M, _stream(stream), ctypes.byref(h)))
+    return Sector(h.value)
+
+
+def ftlm_sector_info(s: Sector) -> dict:
+    n, dim, nb = _U64(), _U64(), ctypes.c_size_t()
+    _check(_lib.ftlm_sector_info(s.handle, ctypes.byref(n), ctypes.byref(dim), ctypes.byref(nb)))
+    return dict(n_reps=n.value, sector_dim=dim.value, device_bytes=nb.value)
+
+
+def ftlm_sector_export(s: Sector):
+    n = ftlm_sector_info(s)["n_reps"]
+    labels = np.zeros(n, dtype=np.uint64)
+    masks = np.zeros((n, 2), dtype=np.uint64)
+    _check(_lib.ftlm_sector_export(s.handle, _ptr(labels), _ptr(masks)))
+    return labels, masks
+
+
+def ftlm_build_block(s: Sector, irrep: int, stream=None) -> Basis:
+    h = ctypes.c_void_p()
+    _check(_lib.ftlm_build_block(s.handle, irrep, _stream(stream), ctypes.byref(h)))
+    return Basis(h.value)
+
+
+def ftlm_build_basis(g: Group, two_s: int, two_M: int, irrep: int, stream=None) -> Basis:
+    h = ctypes.c_void_p()
+    _check(_lib.ftlm_build_basis(g.handle, two_s, two_M, irrep, _stream(stream), ctypes.byref(h)))
+    return Basis(h.value)
+
+
+def ftlm_basis_info(b: Basis) -> dict:
+    n, dim, nb = _U64(), _U64(), ctypes.c_size_t()
+    _check(_lib.ftlm_basis_info(b.handle, ctypes.byref(n), ctypes.byref(dim), ctypes.byref(nb)))
+    return dict(n_reps=n.value, dim=dim.value, device_bytes=nb.value)
+
+
+def ftlm_basis_export(b: Basis):
+    n = ftlm_basis_info(b)["n_reps"]
+    labels = np.zeros(n, dtype=np.uint64)
+    masks = np.zeros((n, 2), dtype=np.uint64)
+    ng = np.zeros(n, dtype=np.uint8)
+    off = np.zeros(n + 1, dtype=np.uint64)
+    _check(_lib.ftlm_basis_export(b.handle, _ptr(labels), _ptr(masks), _ptr(ng), _ptr(off)))
+    return labels, masks, ng, off
+
+
+def ftlm_basis_check(b: Basis, stream=None) -> None:
+    _check(_lib.ftlm_basis_check(b.handle, _stream(stream)))
+
+
+# ---------------------------------------------------------------- H·v, Lanczos, thermo
+
+
+def ftlm_hv(b: Basis, dtype: int, B: int, x, y, stream=None) -> None:
+    """x, y: device pointers (int) or CUDA tensors of shape [dim, B] (float64 for F64, float32 for F32)."""
+    _check(_lib.ftlm_hv(b.handle, dtype, B, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def ftlm_lanczos(b: Basis, dtype: int, R: int, n_steps: int, seed: int, block_id: int, rng: int = GAUSS,
+                 stream=None):
+    alpha = np.zeros((R, n_steps))
+    beta = np.zeros((R, n_steps))
+    steps = np.zeros(R, dtype=np.int32)
+    _check(_lib.ftlm_lanczos(b.handle, dtype, R, n_steps, seed, block_id, rng, _stream(stream), _ptr(alpha),
+                             _ptr(beta), _ptr(steps)))
+    return alpha, beta, steps
+
+
+def ftlm_ritz(alpha, beta, steps, stream=None):
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    steps = np.ascontiguousarray(steps, dtype=np.int32)
+    n, ld = alpha.shape
+    theta = np.zeros((n, ld))
+    w = np.zeros((n, ld))
+    _check(_lib.ftlm_ritz(n, ld, _ptr(steps), _ptr(alpha), _ptr(beta), _ptr(theta), _ptr(w), _stream(stream)))
+    return theta, w
+
+
+def ftlm_thermo(blocks, T, g=1.0, stream=None):
+    """blocks: list of dicts {two_M, d_gamma, dim, alpha[R][ld], beta[R][ld], steps[R]}."""
+    keep = []
+    arr = (ftlm_block * len(blocks))()
+    for i, bl in enumerate(blocks):
+        a = np.ascontiguousarray(bl["alpha"], dtype=np.float64)
+        be = np.ascontiguousarray(bl["beta"], dtype=np.float64)
+        st = np.ascontiguousarray(bl["steps"], dtype=np.int32)
+        keep += [a, be, st]
+        arr[i] = ftlm_block(int(bl["two_M"]), int(bl["d_gamma"]), int(bl["dim"]), a.shape[0], a.shape[1],
+                            _ptr(st), _ptr(a), _ptr(be))
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    out = [np.zeros(len(T)) for _ in range(4)]
+    E0 = np.zeros(1)
+    _check(_lib.ftlm_thermo(len(blocks), arr, len(T), _ptr(T), float(g), *[_ptr(o) for o in out], _ptr(E0),
+                            _stream(stream)))
+    return out[0], out[1], out[2], out[3], float(E0[0])
+
+
+# ---------------------------------------------------------------- profiling
+
+
+def ftlm_profile_enable(on: bool = True) -> None:
+    _check(_lib.ftlm_profile_enable(1 if on else 0))
+
+
+def ftlm_profile_reset() -> None:
+    _check(_lib.ftlm_profile_reset())
+
+
+def ftlm_profile_get() -> dict:
+    p = ftlm_profile()
+    _check(_lib.ftlm_profile_get(ctypes.byref(p)))
+    return dict(kernel_launches=p.kernel_launches, hv_launches=p.hv_launches, hv_ms=p.hv_ms, hv_rows=p.hv_rows)

@@ -1,0 +1,109 @@
+"""C-ABI library checks that need no GPU: symbols, host group module vs oracle, error paths."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.group import Group
+from workloads import cluster
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ftlm():
+    from paper_2607_17429_gb300 import build
+
+    build.build()
+    from paper_2607_17429_gb300 import ftlm as F
+
+    return F
+
+
+def test_library_exports_every_declared_symbol(ftlm):
+    with open(os.path.join(ROOT, "include", "ftlm.h")) as f:
+        text = f.read()
+    declared = set(re.findall(r"^\s*(?:ftlm_status|void|const char \*)\s*(ftlm_\w+)\s*\(", text, re.M))
+    assert len(declared) >= 20
+    lib = ctypes.CDLL(ftlm.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(ftlm.EXPORTED)
+
+
+@pytest.mark.parametrize("name", ["dimer", "ring:5", "tetrahedron", "cuboctahedron", "icosahedron", "dodecahedron",
+                                  "icosidodecahedron", "square:4x4", "square:4x6"])
+def test_builtin_groups_match_oracle(ftlm, name):
+    g = ftlm.ftlm_group_builtin(name)
+    info = ftlm.ftlm_group_info(g)
+    _, perms = ftlm.ftlm_group_irrep(g)
+    bonds, J = ftlm.ftlm_group_bonds(g)
+    c = cluster(name)
+    og = Group(c.gens, c.bonds)
+    assert np.array_equal(perms, og.perms)
+    assert np.array_equal(bonds, c.bonds) and J == 1.0
+    assert list(info["dims"]) == [ir.dim for ir in og.irreps]
+    assert np.abs(info["chars"] - og.char_table).max() < 1e-10
+    for i, ir in enumerate(og.irreps):
+        rho, _ = ftlm.ftlm_group_irrep(g, i)
+        # homomorphism and orthogonality of the library's own matrices
+        assert np.abs(np.einsum("gab,hbc->ghac", rho, rho) - rho[og.mult]).max() < 1e-10
+        assert np.abs(np.einsum("gab,gcb->gac", rho, rho) - np.eye(ir.dim)).max() < 1e-10
+
+
+def test_complex_type_irreps_are_listed_without_matrices(ftlm):
+    """Translations of a 4x4 torus: momenta off {0, pi} have complex characters (Section 3: complex path)."""
+    g = ftlm.ftlm_group_builtin("square:4x4:t")
+    info = ftlm.ftlm_group_info(g)
+    assert info["order"] == 16
+    fs = list(info["fs"])
+    assert fs.count(1) == 4 and fs.count(0) == 6  # k in {0, pi}^2 real; 12 complex momenta in 6 pairs
+    assert sum((2 if f == 0 else 1) * d * d for f, d in zip(fs, info["dims"])) == 16
+    with pytest.raises(ftlm.FtlmError) as e:
+        ftlm.ftlm_group_irrep(g, fs.index(0))
+    assert e.value.status == ftlm.EUNSUPPORTED
+
+
+def test_group_init_from_generators(ftlm):
+    c = cluster("cuboctahedron")
+    g = ftlm.ftlm_group_init(c.gens, c.bonds, J=0.5)
+    assert ftlm.ftlm_group_info(g)["order"] == 48
+    assert ftlm.ftlm_group_bonds(g)[1] == 0.5
+
+
+def test_set_irreps_tabulated(ftlm):
+    c = cluster("icosahedron")
+    og = Group(c.gens, c.bonds)
+    g = ftlm.ftlm_group_init(c.gens, c.bonds)
+    # hand the oracle's matrices over in a scrambled order; the library re-sorts canonically
+    rhos = [ir.rho for ir in og.irreps][::-1]
+    ftlm.ftlm_group_set_irreps(g, rhos)
+    for i, ir in enumerate(og.irreps):
+        rho, _ = ftlm.ftlm_group_irrep(g, i)
+        assert np.array_equal(rho, ir.rho)
+
+
+def test_error_paths(ftlm):
+    c = cluster("icosahedron")
+    with pytest.raises(ftlm.FtlmError) as e:
+        ftlm.ftlm_group_init(np.array([[0, 0, 1]]), np.array([[0, 1]]))
+    assert e.value.status == ftlm.ENOTGROUP
+    with pytest.raises(ftlm.FtlmError) as e:
+        ftlm.ftlm_group_init(c.gens, c.bonds[:-1])
+    assert e.value.status == ftlm.EBONDS
+    with pytest.raises(ftlm.FtlmError) as e:
+        ftlm.ftlm_group_builtin("kagome:36")
+    assert e.value.status == ftlm.EINVAL
+    g = ftlm.ftlm_group_init(c.gens, c.bonds)
+    og = Group(c.gens, c.bonds)
+    bad = [ir.rho.copy() for ir in og.irreps]
+    bad[3][5] *= -1.0  # breaks the homomorphism
+    with pytest.raises(ftlm.FtlmError) as e:
+        ftlm.ftlm_group_set_irreps(g, bad)
+    assert e.value.status == ftlm.EIRREP
+    with pytest.raises(ftlm.FtlmError) as e:
+        ftlm.ftlm_group_set_irreps(g, [ir.rho for ir in og.irreps][:-1])  # incomplete
+    assert e.value.status == ftlm.EIRREP
+    assert "sum of d^2" in ftlm.ftlm_last_error()

@@ -6,4 +6,4 @@ point or space group) and seeded random arrays.  Both the CUDA library and the
 CPU oracle receive these as plain inputs.
 """
 from .clusters import Cluster, cluster, CLUSTER_NAMES  # noqa: F401
-from .seeded import rand_block_vectors  # noqa: F401
+from .seeded import label_keyed_values, rand_block_vectors  # noqa: F401
