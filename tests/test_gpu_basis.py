@@ -11,7 +11,7 @@ from oracle.sector import block_dims, fixed_count, sector_dim
 pytestmark = pytest.mark.gpu
 
 CASES = [("icosahedron", 1, 0), ("icosahedron", 1, 6), ("icosahedron", 1, 12), ("icosahedron", 3, 0),
-         ("cuboctahedron", 1, 0), ("cuboctahedron", 2, 2), ("tetrahedron", 5, 1), ("ring:7", 1, 1),
+         ("cuboctahedron", 1, 0), ("cuboctahedron", 2, 2), ("tetrahedron", 5, 2), ("ring:7", 1, 1),
          ("square:4x4", 1, 0), ("square:4x6", 1, 4), ("dodecahedron", 1, 0), ("dimer", 1, 0),
          ("ring:6", 5, 0), ("cuboctahedron", 3, 12), ("icosahedron", 1, -4)]
 
