@@ -237,6 +237,35 @@ typedef struct {
 ftlm_status ftlm_thermo(int n_blocks, const ftlm_block *blocks, int n_T, const double *T, double g, double *lnZ,
                         double *E, double *C, double *chi, double *E0, void *cuda_stream);
 
+/*
+ * Same thermal sums as ftlm_thermo, for callers that cannot allocate device
+ * memory: code running inside a process whose device memory is entirely
+ * reserved by another allocator or pool (a serving runtime, a framework's
+ * caching allocator), or code that must not trigger the device-wide
+ * synchronisation that cudaMalloc/cudaFree can cause.  The paper has no
+ * counterpart; this is an interface variant of ftlm_thermo.
+ *
+ * Every pointer is a DEVICE pointer owned by the caller, chain-major:
+ *   m [n_chains] steps per chain (0 <= m <= ld), alpha/beta [n_chains][ld]
+ *   (beta[c][j] couples steps j and j+1), weight [n_chains] = mult_M d_Gamma
+ *   D_{M,Gamma} / R of the chain's block (Eq. 14), msq [n_chains] = M^2 of
+ *   that block, T [n_T] > 0; outputs out [4][n_T] = lnZ, E, C, chi and E0 [1].
+ * The intermediate Ritz pairs live in a fixed file-scope device array of
+ * 2 x 2^19 doubles (8 MiB, held by every GPU that loads the library until the
+ * process exits); n_chains * ld above 2^19 (or ld above 512) is rejected with
+ * FTLM_EINVAL before any GPU work.  The call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.  The first call on each device
+ * looks up the array's device address with that device current; make that
+ * first call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents; calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the
+ * caller.  Synchronises cuda_stream before returning; FTLM_EINTERNAL if a
+ * chain's steps exceed ld or the eigensolve does not converge.
+ */
+ftlm_status ftlm_thermo_noalloc(int n_chains, int ld, const int *m, const double *alpha, const double *beta,
+                                const double *weight, const double *msq, int n_T, const double *T, double g,
+                                double *out, double *E0, void *cuda_stream);
+
 /* ---------------------------------------------------------------- profiling */
 
 /*

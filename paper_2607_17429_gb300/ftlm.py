@@ -64,6 +64,7 @@ _SIGS = {
     "ftlm_lanczos": [_P, _I, _I, _I, _U64, _U64, _I, _P, _P, _P, _P],
     "ftlm_ritz": [_I, _I, _P, _P, _P, _P, _P, _P],
     "ftlm_thermo": [_I, _P, _I, _P, ctypes.c_double, _P, _P, _P, _P, _P, _P],
+    "ftlm_thermo_noalloc": [_I, _I, _P, _P, _P, _P, _P, _I, _P, ctypes.c_double, _P, _P, _P],
     "ftlm_profile_enable": [_I],
     "ftlm_profile_reset": [],
     "ftlm_profile_get": [_P],
@@ -307,6 +308,12 @@ def ftlm_thermo(blocks, T, g=1.0, stream=None):
     _check(_lib.ftlm_thermo(len(blocks), arr, len(T), _ptr(T), float(g), *[_ptr(o) for o in out], _ptr(E0),
                             _stream(stream)))
     return out[0], out[1], out[2], out[3], float(E0[0])
+
+
+def ftlm_thermo_noalloc(n_chains, ld, m, alpha, beta, weight, msq, n_T, T, g, out, E0, stream=None) -> None:
+    """All array arguments are device pointers (ints) or CUDA tensors; see include/ftlm.h."""
+    _check(_lib.ftlm_thermo_noalloc(int(n_chains), int(ld), _ptr(m), _ptr(alpha), _ptr(beta), _ptr(weight),
+                                    _ptr(msq), int(n_T), _ptr(T), float(g), _ptr(out), _ptr(E0), _stream(stream)))
 
 
 # ---------------------------------------------------------------- profiling
