@@ -118,7 +118,20 @@ def run_ours(args, rank, world):
     n_ir = len(F.ftlm_group_info(group)["dims"])
     dims_g = F.ftlm_group_info(group)["dims"]
 
-    def step(grp, dt):
+    def step_multi(grp, dt):
+        """Batched form: all 10 irrep blocks through one multi-block H·v launch per Lanczos step."""
+        sec = F.ftlm_build_sector(grp, TWO_S, TWO_M, stream)
+        mb = F.ftlm_build_multiblock(sec, list(range(n_ir)), stream)
+        dims = F.ftlm_multiblock_info(mb)["dims"]
+        a, b, st = F.ftlm_lanczos_multi(mb, dt, R, N_STEPS, SEED, [64 * TWO_M + ir for ir in range(n_ir)], F.GAUSS,
+                                        stream)
+        blocks = [dict(two_M=TWO_M, d_gamma=int(dims_g[k]), dim=dims[k], alpha=a[k], beta=b[k], steps=st[k])
+                  for k in range(n_ir)]
+        states = sum(dims[k] * int(st[k].sum()) for k in range(n_ir))
+        return states, F.ftlm_thermo(blocks, T_GRID, 1.0, stream)
+
+    def step_single(grp, dt):
+        """Plain form: one block at a time, one H·v launch per block and Lanczos step."""
         sec = F.ftlm_build_sector(grp, TWO_S, TWO_M, stream)
         blocks, states = [], 0
         for ir in range(n_ir):
@@ -127,12 +140,14 @@ def run_ours(args, rank, world):
             a, b, st = F.ftlm_lanczos(blk, dt, R, N_STEPS, SEED, 64 * TWO_M + ir, F.GAUSS, stream)
             blocks.append(dict(two_M=TWO_M, d_gamma=int(dims_g[ir]), dim=dim, alpha=a, beta=b, steps=st))
             states += dim * int(st.sum())
-        out = F.ftlm_thermo(blocks, T_GRID, 1.0, stream)
-        return states, out
+        return states, F.ftlm_thermo(blocks, T_GRID, 1.0, stream)
 
-    def timed(dt, K, W):
+    step = step_multi
+
+    def timed(dt, K, W, fn=None):
+        fn = fn or step
         for _ in range(W):
-            step(group, dt)
+            fn(group, dt)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -144,7 +159,7 @@ def run_ours(args, rank, world):
         states = 0
         out = None
         for _ in range(K):
-            s, out = step(group, dt)
+            s, out = fn(group, dt)
             states += s
         e1.record(stream)
         torch.cuda.synchronize()
@@ -163,17 +178,34 @@ def run_ours(args, rank, world):
     value = states * world / (ms_all / 1e3) / 1e9  # replicas: every rank runs the same workload
     res = {"ms": ms, "states": states, "prof": prof, "out": out, "clocks": clk.summary(), "value": value,
            "ms_all": ms_all}
+    # algorithmic counts of one multi-block H·v launch (for the roofline)
+    sec = F.ftlm_build_sector(group, TWO_S, TWO_M, stream)
+    labels, _ = F.ftlm_sector_export(sec)
+    mb = F.ftlm_build_multiblock(sec, list(range(n_ir)), stream)
+    res.update(flips=_flip_count(labels, bonds), G=F.ftlm_group_info(group)["order"],
+               sum_d2=int(sum(int(d) ** 2 for d in dims_g)), rows=sum(F.ftlm_multiblock_info(mb)["dims"]) * R,
+               n_reps=len(labels), K=n_ir)
+    del mb, sec
 
-    # FP64 companion run (mixed vs FP64 is part of the metric)
+    # FP64 companions: the plain one-block-at-a-time form and the batched form (mixed vs FP64 error)
     fp64 = None
     if not args.skip_fp64 and dtype == F.F32:
-        ms64, st64, prof64, out64 = timed(F.F64, max(1, args.steps), 1)
-        fp64 = {"value": st64 / (ms64 / 1e3) / 1e9, "ms_per_step": ms64 / max(1, args.steps),
-                "hv_ms_per_launch": prof64["hv_ms"] / max(1, prof64["hv_launches"]),
-                "E0": out64[4], "dE0_mixed_vs_fp64": out[4] - out64[4],
-                "max_dC_over_Cmax": float(np.abs(out[2] - out64[2])[T_GRID >= 0.05].max() / out64[2].max()),
-                "max_dchi_over_chimax": (float(np.abs(out[3] - out64[3])[T_GRID >= 0.05].max() / out64[3].max())
-                                         if out64[3].max() > 0 else 0.0)}
+        fp64 = {}
+        for name, fn in (("plain_single_block", step_single), ("batched", step_multi)):
+            ms64, st64, prof64, out64 = timed(F.F64, 1, 1, fn)
+            fp64[name] = {"value": st64 / (ms64 / 1e3) / 1e9, "ms_per_step": ms64,
+                          "blocks_per_hour": 10 / (ms64 / 1e3) * 3600.0,
+                          "hv_ms_per_launch": prof64["hv_ms"] / max(1, prof64["hv_launches"]), "E0": out64[4]}
+        ref = out64  # FP64 batched
+        sel = T_GRID >= 0.05
+        fp64["mixed_vs_fp64"] = {
+            "dE0_rel": abs(out[4] - ref[4]) / abs(ref[4]),
+            "max_dC_over_Cmax": float(np.abs(out[2] - ref[2])[sel].max() / ref[2].max()),
+            "max_dchi_over_chimax": (float(np.abs(out[3] - ref[3])[sel].max() / ref[3].max())
+                                     if ref[3].max() > 0 else 0.0),
+            "max_dlnZ_rel": float(np.abs((out[0] - ref[0]) / ref[0]).max())}
+        fp64["batched_mixed_over_plain_fp64_blocks_per_hour"] = (
+            (10 * args.steps / (ms / 1e3)) / (10 / (fp64["plain_single_block"]["ms_per_step"] / 1e3)))
 
     # e2e: public API from host buffers, wall clock, copies inside
     torch.cuda.synchronize()
@@ -193,13 +225,59 @@ def run_ours(args, rank, world):
     return res
 
 
-def hv_roofline(prof, dtype_name):
-    """Dominant kernel: H·v.  Algorithmic HBM bytes per launch (compulsory traffic)."""
+def _flip_count(labels, bonds):
+    """Admissible s=1/2 ladder flips summed over representatives (antiparallel bonds)."""
+    lab = labels.astype(np.uint64)
+    total = 0
+    for i, j in bonds:
+        total += int(np.count_nonzero(((lab >> np.uint64(i)) ^ (lab >> np.uint64(j))) & np.uint64(1)))
+    return total
+
+
+def _traffic_record(kernel, dtype_name):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2607_17429_gb300", "csrc", "hv_multi_impl.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
+    try:
+        for ln in open(path):
+            p = ln.split()
+            if len(p) >= 4 and p[0] == kernel and p[1] == dtype_name and p[3] == sha:
+                return float(p[2])
+    except OSError:
+        pass
+    return None
+
+
+def hv_roofline(prof, dtype_name, flips, G, sum_d2, B, rows, n_reps, K, esize):
+    """Roofline of the dominant kernel (multi-block H·v), per launch.
+
+    alu: algorithmic lane-operations = flips*|G|*2 (image and min per candidate of the
+         representative search) + flips*sum_k d_k^2*B (contraction FMAs), against the
+         issue peak 152 SMs x 128 lanes x 2.07 GHz.
+    hbm: compulsory bytes = x read once + y written once (sum_k dim_k*B*esize each) +
+         representative tables (n_reps*(8 + 2 + 4K)), against the measured copy bandwidth.
+    The larger fraction is the binding one.
+    """
     pk, which = peaks()
     if prof["hv_launches"] == 0:
         return None
-    avg_ms = prof["hv_ms"] / prof["hv_launches"]
-    return {"avg_ms": avg_ms, "peak_source": which, "pk": pk}
+    t = prof["hv_ms"] / prof["hv_launches"] / 1e3
+    ops = flips * G * 2 + flips * sum_d2 * B
+    alu_peak = 152 * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
+    byt = 2 * rows * esize + n_reps * (8 + 2 + 4 * K)
+    hbm_peak = float(pk["hbm_gbs"]) * 1e9
+    alu = {"bound": "alu", "achieved": ops / t / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
+           "frac": ops / t / alu_peak, "traffic": _traffic_record("hv_multi_kernel", dtype_name),
+           "algorithmic_per_launch": ops, "peak_source": "derived: 152 SMs x 128 lanes x max SM clock"}
+    hbm = {"bound": "hbm", "achieved": byt / t / 1e9, "peak": hbm_peak / 1e9, "unit": "GB/s",
+           "frac": byt / t / hbm_peak, "traffic": alu["traffic"], "algorithmic_per_launch": byt,
+           "peak_source": f"{which} MEASURED_PEAKS.json hbm_gbs" if which == "measured" else "fallback 6.8 TB/s"}
+    main, alt = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
+    main["avg_launch_ms"] = t * 1e3
+    return main, alt
 
 
 def cpu_baseline(budget_s=12.0):
@@ -271,7 +349,8 @@ def main():
     if rank != 0:
         return
     prof = res["prof"]
-    rl = hv_roofline(prof, args.dtype)
+    rl = hv_roofline(prof, args.dtype, res["flips"], res["G"], res["sum_d2"], R, res["rows"], res["n_reps"],
+                     res["K"], 4 if args.dtype == "f32" else 8)
     line = {
         "metric": "sym-adapted H·v Gstates/s (mixed FP32 vectors, FP64 alpha/beta)" if args.dtype == "f32"
         else "sym-adapted H·v Gstates/s (FP64)",
@@ -284,7 +363,9 @@ def main():
         "blocks_per_hour": 10 * args.steps / (res["ms_all"] / 1e3) * 3600.0 * world,
         "gpu_launches": int(prof["kernel_launches"]),
         "hv_launches": int(prof["hv_launches"]),
-        "hv_ms_per_launch": rl["avg_ms"] if rl else None,
+        "hv_ms_per_launch": prof["hv_ms"] / max(1, prof["hv_launches"]),
+        "roofline": rl[0] if rl else None,
+        "roofline_other": rl[1] if rl else None,
         "E0": res["out"][4],
         "e2e": res["e2e"],
         "clocks": res["clocks"],

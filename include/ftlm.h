@@ -60,6 +60,7 @@ typedef enum { FTLM_GAUSS = 0, FTLM_RADEMACHER = 1 } ftlm_rng;
 typedef struct ftlm_group ftlm_group;   /* host: permutations, multiplication table, irreps, bonds */
 typedef struct ftlm_sector ftlm_sector; /* device: representatives, stabilizers, lookup index of one (s, M) */
 typedef struct ftlm_basis ftlm_basis;   /* device: one (s, M, Gamma) block on top of a sector */
+typedef struct ftlm_multiblock ftlm_multiblock; /* device: several blocks of one sector, one H·v launch */
 
 /* ---------------------------------------------------------------- group (host) */
 
@@ -182,6 +183,29 @@ ftlm_status ftlm_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x,
 /* Synchronise cuda_stream and report (then clear) the basis's device error flag. */
 ftlm_status ftlm_basis_check(const ftlm_basis *b, void *cuda_stream);
 
+/*
+ * Several irrep blocks of one sector prepared for a shared H·v launch.  The
+ * representative search and lookup of a flipped state are irrep independent
+ * (Section 3 builds that part once per sector), so ftlm_hv_multi runs them
+ * once per representative and then applies Eq. 15's contraction for every
+ * block.  irreps: [n_blocks] indices (1 <= n_blocks <= 16); every block must
+ * have dim < 2^32.  The set owns its blocks and keeps the sector alive.
+ */
+ftlm_status ftlm_build_multiblock(const ftlm_sector *s, int n_blocks, const int *irreps, void *cuda_stream,
+                                  ftlm_multiblock **out);
+ftlm_status ftlm_multiblock_info(const ftlm_multiblock *mb, int *n_blocks, uint64_t *dims, size_t *device_bytes);
+/* Borrowed handle of block k (valid while the set lives), e.g. for ftlm_basis_export or ftlm_hv. */
+ftlm_status ftlm_multiblock_block(const ftlm_multiblock *mb, int k, const ftlm_basis **out);
+void ftlm_multiblock_free(ftlm_multiblock *mb);
+
+/*
+ * y_k = H x_k for every block k of the set in one launch (same result as
+ * ftlm_hv per block).  x, y: host arrays of n_blocks device pointers, block k's
+ * vectors [dim_k][B] of the chosen dtype.  Asynchronous on cuda_stream.
+ */
+ftlm_status ftlm_hv_multi(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, const void *const *x, void *const *y,
+                          void *cuda_stream);
+
 /* ---------------------------------------------------------------- Lanczos / FTLM */
 
 /*
@@ -204,6 +228,17 @@ ftlm_status ftlm_basis_check(const ftlm_basis *b, void *cuda_stream);
 ftlm_status ftlm_lanczos(const ftlm_basis *b, ftlm_dtype dtype, int R, int n_steps, uint64_t seed,
                          uint64_t block_id, ftlm_rng rng, void *cuda_stream, double *alpha, double *beta,
                          int *steps_done);
+
+/*
+ * ftlm_lanczos on every block of a multi-block set in lockstep: each step is
+ * one ftlm_hv_multi launch plus the per-block recurrence kernels.  Block k
+ * draws its start vectors with block_ids[k]; results equal ftlm_lanczos per
+ * block up to rounding.  alpha, beta: host [n_blocks][R][n_steps];
+ * steps_done: host [n_blocks][R].
+ */
+ftlm_status ftlm_lanczos_multi(const ftlm_multiblock *mb, ftlm_dtype dtype, int R, int n_steps, uint64_t seed,
+                               const uint64_t *block_ids, ftlm_rng rng, void *cuda_stream, double *alpha,
+                               double *beta, int *steps_done);
 
 /*
  * Ritz values and weights of tridiagonal matrices on the GPU in FP64 (implicit

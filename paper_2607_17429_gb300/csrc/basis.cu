@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "contract.cuh"
 
 namespace ftlm {
 
@@ -488,20 +489,27 @@ ftlm_status build_block_impl(ftlm_sector *s, int irrep, cudaStream_t stream, ftl
     }
     b->h_ntab = ntab;
     std::vector<float> Vf(V.begin(), V.end()), sqf(sq.begin(), sq.end());
-    std::vector<double> rhoT((size_t)G * d * d);
+    b->rho_elems = rho_table_elems<double>(G, d);
+    b->rho_elemsf = rho_table_elems<float>(G, d);
+    std::vector<double> rhoT(b->rho_elems, 0.0);
+    std::vector<float> rhoTf(b->rho_elemsf, 0.0f);
+    const int RP = rho_row(d);
     for (int g = 0; g < G; ++g)
         for (int r = 0; r < d; ++r)
-            for (int c = 0; c < d; ++c) rhoT[((size_t)g * d + r) * d + c] = ir.rho[((size_t)g * d + c) * d + r];
-    std::vector<float> rhoTf(rhoT.begin(), rhoT.end());
+            for (int c = 0; c < d; ++c) {
+                const double v = ir.rho[((size_t)g * d + c) * d + r];
+                rhoT[((size_t)g * d + r) * RP + c] = v;
+                rhoTf[((size_t)g * d + r) * RP + c] = (float)v;
+            }
     FTLM_CUDA(cudaMalloc((void **)&b->d_ntab, ns));
     FTLM_CUDA(cudaMalloc((void **)&b->d_sqrtS, ns * 8));
     FTLM_CUDA(cudaMalloc((void **)&b->d_sqrtSf, ns * 4));
     FTLM_CUDA(cudaMalloc((void **)&b->d_V, V.size() * 8));
     FTLM_CUDA(cudaMalloc((void **)&b->d_Vf, V.size() * 4));
     FTLM_CUDA(cudaMalloc((void **)&b->d_rhoT, rhoT.size() * 8));
-    FTLM_CUDA(cudaMalloc((void **)&b->d_rhoTf, rhoT.size() * 4));
+    FTLM_CUDA(cudaMalloc((void **)&b->d_rhoTf, rhoTf.size() * 4));
     FTLM_CUDA(cudaMalloc((void **)&b->d_off, (s->n_reps + 1) * 8));
-    b->device_bytes = ns * 13 + V.size() * 12 + rhoT.size() * 12 + (s->n_reps + 1) * 8;
+    b->device_bytes = ns * 13 + V.size() * 12 + rhoT.size() * 8 + rhoTf.size() * 4 + (s->n_reps + 1) * 8;
     FTLM_CUDA(cudaMemcpyAsync(b->d_ntab, ntab.data(), ns, cudaMemcpyHostToDevice, stream));
     FTLM_CUDA(cudaMemcpyAsync(b->d_sqrtS, sq.data(), ns * 8, cudaMemcpyHostToDevice, stream));
     FTLM_CUDA(cudaMemcpyAsync(b->d_sqrtSf, sqf.data(), ns * 4, cudaMemcpyHostToDevice, stream));
@@ -509,10 +517,82 @@ ftlm_status build_block_impl(ftlm_sector *s, int irrep, cudaStream_t stream, ftl
     FTLM_CUDA(cudaMemcpyAsync(b->d_Vf, Vf.data(), Vf.size() * 4, cudaMemcpyHostToDevice, stream));
     FTLM_CUDA(cudaMemcpyAsync(b->d_rhoT, rhoT.data(), rhoT.size() * 8, cudaMemcpyHostToDevice, stream));
     FTLM_CUDA(cudaMemcpyAsync(b->d_rhoTf, rhoTf.data(), rhoTf.size() * 4, cudaMemcpyHostToDevice, stream));
+    FTLM_CUDA(cudaStreamSynchronize(stream));  // host staging vectors go out of scope
     uint64_t dim = 0;
     ftlm_status st = exclusive_scan(NGammaOf{s->d_stab_id, b->d_ntab}, s->n_reps, b->d_off, stream, &dim);
     if (st != FTLM_OK) return st;
     b->dim = dim;
+    return FTLM_OK;
+}
+
+__global__ void interleave_offsets(const uint64_t *const *offs, int K, uint64_t n_reps, uint64_t *offm) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_reps) return;
+    for (int k = 0; k < K; ++k) offm[i * K + k] = offs[k][i];
+}
+
+void free_multiblock(ftlm_multiblock *mb) {
+    if (!mb) return;
+    for (auto *b : mb->blocks) free_block(b);
+    cudaFree(mb->d_offm);
+    cudaFree(mb->d_ntab);
+    cudaFree(mb->d_rhoT);
+    cudaFree(mb->d_rhoTf);
+    if (mb->sec) sector_release(mb->sec);
+    delete mb;
+}
+
+ftlm_status build_multiblock_impl(ftlm_sector *s, int n, const int *irreps, cudaStream_t stream,
+                                  ftlm_multiblock *mb) {
+    mb->K = n;
+    const size_t ns = s->stab_elems.size();
+    std::vector<uint8_t> ntab((size_t)n * ns);
+    std::vector<double> rho;
+    std::vector<float> rhof;
+    for (int k = 0; k < n; ++k) {
+        ftlm_basis *b = new (std::nothrow) ftlm_basis();
+        if (!b) return fail(FTLM_ENOMEM, "host allocation failed");
+        s->refs.fetch_add(1);
+        b->sec = s;
+        mb->blocks.push_back(b);
+        ftlm_status st = build_block_impl(s, irreps[k], stream, b);
+        if (st != FTLM_OK) return st;
+        std::copy(b->h_ntab.begin(), b->h_ntab.end(), ntab.begin() + (size_t)k * ns);
+        const Irrep &ir = s->grp.irreps[irreps[k]];
+        const int d = ir.dim, G = s->G, RP = rho_row(d);
+        mb->d.push_back(d);
+        mb->rho_off.push_back((int)rho.size());
+        mb->rho_offf.push_back((int)rhof.size());
+        rho.resize(rho.size() + rho_table_elems<double>(G, d), 0.0);
+        rhof.resize(rhof.size() + rho_table_elems<float>(G, d), 0.0f);
+        for (int g = 0; g < G; ++g)
+            for (int r = 0; r < d; ++r)
+                for (int c = 0; c < d; ++c) {
+                    const double v = ir.rho[((size_t)g * d + c) * d + r];
+                    rho[mb->rho_off.back() + ((size_t)g * d + r) * RP + c] = v;
+                    rhof[mb->rho_offf.back() + ((size_t)g * d + r) * RP + c] = (float)v;
+                }
+        mb->device_bytes += b->device_bytes;
+    }
+    mb->rho_total = (int)rho.size();
+    mb->rho_totalf = (int)rhof.size();
+    std::vector<const uint64_t *> offs(n);
+    for (int k = 0; k < n; ++k) offs[k] = mb->blocks[k]->d_off;
+    DevBuf<const uint64_t *> d_offs;
+    FTLM_CUDA(d_offs.alloc(n));
+    FTLM_CUDA(cudaMemcpyAsync(d_offs.p, offs.data(), n * sizeof(void *), cudaMemcpyHostToDevice, stream));
+    FTLM_CUDA(cudaMalloc((void **)&mb->d_offm, s->n_reps * n * 8 + 8));
+    FTLM_CUDA(cudaMalloc((void **)&mb->d_ntab, ntab.size()));
+    FTLM_CUDA(cudaMalloc((void **)&mb->d_rhoT, rho.size() * 8));
+    FTLM_CUDA(cudaMalloc((void **)&mb->d_rhoTf, rhof.size() * 4));
+    mb->device_bytes += s->n_reps * n * 8 + ntab.size() + rho.size() * 8 + rhof.size() * 4;
+    FTLM_CUDA(cudaMemcpyAsync(mb->d_ntab, ntab.data(), ntab.size(), cudaMemcpyHostToDevice, stream));
+    FTLM_CUDA(cudaMemcpyAsync(mb->d_rhoT, rho.data(), rho.size() * 8, cudaMemcpyHostToDevice, stream));
+    FTLM_CUDA(cudaMemcpyAsync(mb->d_rhoTf, rhof.data(), rhof.size() * 4, cudaMemcpyHostToDevice, stream));
+    count_launch();
+    interleave_offsets<<<(unsigned)((s->n_reps + 255) / 256), 256, 0, stream>>>(d_offs.p, n, s->n_reps, mb->d_offm);
+    FTLM_CUDA(cudaGetLastError());
+    FTLM_CUDA(cudaStreamSynchronize(stream));
     return FTLM_OK;
 }
 
@@ -619,6 +699,43 @@ ftlm_status ftlm_basis_export(const ftlm_basis *b, uint64_t *labels, uint64_t *s
 }
 
 void ftlm_basis_free(ftlm_basis *b) { free_block(b); }
+
+ftlm_status ftlm_build_multiblock(const ftlm_sector *s_const, int n_blocks, const int *irreps, void *cuda_stream,
+                                  ftlm_multiblock **out) {
+    if (!s_const || !irreps || !out) return fail(FTLM_EINVAL, "NULL argument");
+    if (n_blocks < 1 || n_blocks > 16) return fail(FTLM_EINVAL, "n_blocks must be in 1..16");
+    *out = nullptr;
+    ftlm_sector *s = const_cast<ftlm_sector *>(s_const);
+    ftlm_multiblock *mb = new (std::nothrow) ftlm_multiblock();
+    if (!mb) return fail(FTLM_ENOMEM, "host allocation failed");
+    s->refs.fetch_add(1);
+    mb->sec = s;
+    ftlm_status st = build_multiblock_impl(s, n_blocks, irreps, (cudaStream_t)cuda_stream, mb);
+    if (st != FTLM_OK) {
+        cudaStreamSynchronize((cudaStream_t)cuda_stream);
+        free_multiblock(mb);
+        return st;
+    }
+    *out = mb;
+    return FTLM_OK;
+}
+
+ftlm_status ftlm_multiblock_info(const ftlm_multiblock *mb, int *n_blocks, uint64_t *dims, size_t *device_bytes) {
+    if (!mb) return fail(FTLM_EINVAL, "multiblock is NULL");
+    if (n_blocks) *n_blocks = mb->K;
+    if (dims)
+        for (int k = 0; k < mb->K; ++k) dims[k] = mb->blocks[k]->dim;
+    if (device_bytes) *device_bytes = mb->device_bytes + mb->sec->device_bytes;
+    return FTLM_OK;
+}
+
+ftlm_status ftlm_multiblock_block(const ftlm_multiblock *mb, int k, const ftlm_basis **out) {
+    if (!mb || !out || k < 0 || k >= mb->K) return fail(FTLM_EINVAL, "bad arguments");
+    *out = mb->blocks[k];
+    return FTLM_OK;
+}
+
+void ftlm_multiblock_free(ftlm_multiblock *mb) { free_multiblock(mb); }
 
 ftlm_status ftlm_basis_check(const ftlm_basis *b, void *cuda_stream) {
     if (!b) return fail(FTLM_EINVAL, "basis is NULL");

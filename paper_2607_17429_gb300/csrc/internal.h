@@ -89,10 +89,25 @@ struct ftlm_basis {
     float *d_sqrtSf = nullptr;
     double *d_V = nullptr;
     float *d_Vf = nullptr;
-    // rho(g)^T per element, [G][d][d]: rhoT[g][b][c] = rho(g)[c][b]
+    // rho(g)^T per element with padded rows, [G][d][rho_row(d)]: rhoT[g][b][c] = rho(g)[c][b]
     double *d_rhoT = nullptr;
     float *d_rhoTf = nullptr;
+    int rho_elems = 0, rho_elemsf = 0;  // padded table sizes (FP64, FP32)
     std::vector<uint8_t> h_ntab;
+    size_t device_bytes = 0;
+};
+
+// Several irrep blocks of one sector sharing one H·v launch (basis.cu, hv_multi_*.cu).
+struct ftlm_multiblock {
+    ftlm_sector *sec = nullptr;
+    int K = 0;
+    std::vector<ftlm_basis *> blocks;  // owned
+    uint64_t *d_offm = nullptr;        // [n_reps][K] row offsets, interleaved
+    uint8_t *d_ntab = nullptr;         // [K][n_sid]
+    double *d_rhoT = nullptr;          // blocks' padded rho(g)^T tables concatenated
+    float *d_rhoTf = nullptr;
+    int rho_total = 0, rho_totalf = 0;
+    std::vector<int> d, rho_off, rho_offf;
     size_t device_bytes = 0;
 };
 

@@ -17,6 +17,10 @@ namespace ftlm {
 
 ftlm_status hv_launch_f64(const ftlm_basis *bs, int B, const double *x, double *y, cudaStream_t stream);
 ftlm_status hv_launch_f32(const ftlm_basis *bs, int B, const float *x, float *y, cudaStream_t stream);
+ftlm_status hv_multi_launch_f64(const ftlm_multiblock *mb, int B, const double *const *x, double *const *y,
+                               cudaStream_t stream);
+ftlm_status hv_multi_launch_f32(const ftlm_multiblock *mb, int B, const float *const *x, float *const *y,
+                               cudaStream_t stream);
 
 namespace {
 
@@ -267,6 +271,122 @@ ftlm_status lanczos_impl(const ftlm_basis *bs, int R, int n_steps, uint64_t seed
     return FTLM_OK;
 }
 
+template <typename VT>
+ftlm_status hv_multi_any(const ftlm_multiblock *mb, int B, const VT *const *x, VT *const *y, cudaStream_t st);
+template <>
+ftlm_status hv_multi_any<double>(const ftlm_multiblock *mb, int B, const double *const *x, double *const *y,
+                                 cudaStream_t st) {
+    return hv_multi_launch_f64(mb, B, x, y, st);
+}
+template <>
+ftlm_status hv_multi_any<float>(const ftlm_multiblock *mb, int B, const float *const *x, float *const *y,
+                                cudaStream_t st) {
+    return hv_multi_launch_f32(mb, B, x, y, st);
+}
+
+// Lanczos on every block of a multi-block set in lockstep: one multi-block H·v
+// per step, then the per-block recurrence kernels.
+template <typename VT>
+ftlm_status lanczos_multi_impl(const ftlm_multiblock *mb, int R, int n_steps, uint64_t seed, const uint64_t *ids,
+                               int rng, cudaStream_t stream, double *alpha, double *beta, int *steps_done) {
+    const int K = mb->K;
+    const int Bmax = std::min(R, kMaxB);
+    for (size_t i = 0; i < (size_t)K * R; ++i) steps_done[i] = 0;
+    for (size_t i = 0; i < (size_t)K * R * n_steps; ++i) alpha[i] = beta[i] = 0.0;
+    std::vector<uint64_t> dim(K);
+    std::vector<int> m_max(K);
+    int m_all = 0;
+    for (int k = 0; k < K; ++k) {
+        dim[k] = mb->blocks[k]->dim;
+        m_max[k] = (int)std::min<uint64_t>((uint64_t)n_steps, dim[k]);
+        m_all = std::max(m_all, m_max[k]);
+    }
+    std::vector<DevBuf<VT>> vec(3 * K);
+    for (int k = 0; k < K; ++k)
+        for (int q = 0; q < 3; ++q) FTLM_CUDA(vec[3 * k + q].alloc(std::max<uint64_t>(dim[k], 1) * Bmax));
+    const size_t per_state = (size_t)2 * n_steps * Bmax + 2 * Bmax;
+    DevBuf<double> partials, dstate;
+    DevBuf<int> istate;
+    FTLM_CUDA(partials.alloc((size_t)kRedBlocks * Bmax));
+    FTLM_CUDA(dstate.alloc(per_state * K));
+    FTLM_CUDA(istate.alloc((size_t)2 * Bmax * K));
+    std::vector<LzState> st(K);
+    for (int k = 0; k < K; ++k) {
+        double *base = dstate.p + per_state * k;
+        st[k].alpha = base;
+        st[k].beta = base + (size_t)n_steps * Bmax;
+        st[k].beta_prev = base + (size_t)2 * n_steps * Bmax;
+        st[k].scale = st[k].beta_prev + Bmax;
+        st[k].active = istate.p + (size_t)2 * Bmax * k;
+        st[k].steps = st[k].active + Bmax;
+    }
+    std::vector<double> ha((size_t)n_steps * Bmax), hb((size_t)n_steps * Bmax);
+    std::vector<int> hs(Bmax);
+    const int scale_blocks = kNumSMs * 8;
+    std::vector<const VT *> xs(K);
+    std::vector<VT *> ys(K), vp(K), v(K), w(K);
+    for (int chain0 = 0; chain0 < R; chain0 += Bmax) {
+        const int B = std::min(Bmax, R - chain0);
+        FTLM_CUDA(cudaMemsetAsync(dstate.p, 0, per_state * K * sizeof(double), stream));
+        for (int k = 0; k < K; ++k) {
+            vp[k] = vec[3 * k].p;
+            v[k] = vec[3 * k + 1].p;
+            w[k] = vec[3 * k + 2].p;
+            if (dim[k] == 0) continue;
+            FTLM_CUDA(cudaMemsetAsync(vp[k], 0, dim[k] * B * sizeof(VT), stream));
+            count_launch(3);
+            lz_random<VT><<<kRedBlocks, kRedThreads, 0, stream>>>(v[k], dim[k], B, B, (uint32_t)chain0, (uint32_t)seed,
+                                                                  (uint32_t)ids[k], rng, partials.p);
+            fin_norm<<<1, 32, 0, stream>>>(partials.p, B, st[k]);
+            lz_scale<VT><<<scale_blocks, 256, 0, stream>>>(v[k], dim[k], B, st[k]);
+            FTLM_CUDA(cudaGetLastError());
+        }
+        for (int j = 0; j < m_all; ++j) {
+            for (int k = 0; k < K; ++k) {
+                xs[k] = v[k];
+                ys[k] = w[k];
+            }
+            ftlm_status sst = hv_multi_any<VT>(mb, B, xs.data(), ys.data(), stream);
+            if (sst != FTLM_OK) return sst;
+            for (int k = 0; k < K; ++k) {
+                if (j >= m_max[k]) continue;
+                count_launch(5);
+                lz_dot<VT><<<kRedBlocks, kRedThreads, 0, stream>>>(v[k], w[k], dim[k], B, partials.p);
+                fin_alpha<<<1, 32, 0, stream>>>(partials.p, B, j, st[k]);
+                lz_update<VT><<<kRedBlocks, kRedThreads, 0, stream>>>(w[k], v[k], vp[k], dim[k], B, j, st[k],
+                                                                      partials.p);
+                fin_beta<<<1, 32, 0, stream>>>(partials.p, B, j, m_max[k], sizeof(VT) == 8 ? 1e-12 : 1e-6, st[k]);
+                lz_scale<VT><<<scale_blocks, 256, 0, stream>>>(w[k], dim[k], B, st[k]);
+                FTLM_CUDA(cudaGetLastError());
+                VT *t = vp[k];
+                vp[k] = v[k];
+                v[k] = w[k];
+                w[k] = t;
+            }
+        }
+        for (int k = 0; k < K; ++k) {
+            if (dim[k] == 0) continue;
+            FTLM_CUDA(cudaMemcpyAsync(ha.data(), st[k].alpha, (size_t)n_steps * B * 8, cudaMemcpyDeviceToHost, stream));
+            FTLM_CUDA(cudaMemcpyAsync(hb.data(), st[k].beta, (size_t)n_steps * B * 8, cudaMemcpyDeviceToHost, stream));
+            FTLM_CUDA(cudaMemcpyAsync(hs.data(), st[k].steps, (size_t)B * 4, cudaMemcpyDeviceToHost, stream));
+            FTLM_CUDA(cudaStreamSynchronize(stream));
+            for (int b = 0; b < B; ++b) {
+                const int r = chain0 + b;
+                const size_t kr = (size_t)k * R + r;
+                steps_done[kr] = hs[b];
+                for (int jj = 0; jj < hs[b]; ++jj) {
+                    alpha[kr * n_steps + jj] = ha[(size_t)jj * B + b];
+                    beta[kr * n_steps + jj] = hb[(size_t)jj * B + b];
+                }
+            }
+        }
+        int err = 0;
+        FTLM_CUDA(cudaMemcpy(&err, mb->sec->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) return fail(FTLM_EINTERNAL, "device bounds check tripped in H·v (code %d)", err);
+    }
+    return FTLM_OK;
+}
+
 }  // namespace
 }  // namespace ftlm
 
@@ -292,6 +412,33 @@ ftlm_status ftlm_lanczos(const ftlm_basis *b, ftlm_dtype dtype, int R, int n_ste
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (dtype == FTLM_F64) return lanczos_impl<double>(b, R, n_steps, seed, block_id, rng, st, alpha, beta, steps_done);
     if (dtype == FTLM_F32) return lanczos_impl<float>(b, R, n_steps, seed, block_id, rng, st, alpha, beta, steps_done);
+    return fail(FTLM_EINVAL, "unknown dtype");
+}
+
+ftlm_status ftlm_hv_multi(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, const void *const *x,
+                          void *const *y, void *cuda_stream) {
+    if (!mb || !x || !y) return fail(FTLM_EINVAL, "NULL argument");
+    if (B < 1 || B > kMaxB) return fail(FTLM_EINVAL, "B must be in 1..%d", kMaxB);
+    for (int k = 0; k < mb->K; ++k)
+        if (!x[k] || !y[k]) return fail(FTLM_EINVAL, "NULL vector for block %d", k);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (dtype == FTLM_F64)
+        return hv_multi_launch_f64(mb, B, (const double *const *)x, (double *const *)y, st);
+    if (dtype == FTLM_F32) return hv_multi_launch_f32(mb, B, (const float *const *)x, (float *const *)y, st);
+    return fail(FTLM_EINVAL, "unknown dtype");
+}
+
+ftlm_status ftlm_lanczos_multi(const ftlm_multiblock *mb, ftlm_dtype dtype, int R, int n_steps, uint64_t seed,
+                               const uint64_t *block_ids, ftlm_rng rng, void *cuda_stream, double *alpha,
+                               double *beta, int *steps_done) {
+    if (!mb || !block_ids || !alpha || !beta || !steps_done) return fail(FTLM_EINVAL, "NULL argument");
+    if (R < 1 || n_steps < 1 || n_steps > kMaxSteps) return fail(FTLM_EINVAL, "R >= 1 and 1 <= n_steps <= 512");
+    if (rng != FTLM_GAUSS && rng != FTLM_RADEMACHER) return fail(FTLM_EINVAL, "unknown rng");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (dtype == FTLM_F64)
+        return lanczos_multi_impl<double>(mb, R, n_steps, seed, block_ids, rng, st, alpha, beta, steps_done);
+    if (dtype == FTLM_F32)
+        return lanczos_multi_impl<float>(mb, R, n_steps, seed, block_ids, rng, st, alpha, beta, steps_done);
     return fail(FTLM_EINVAL, "unknown dtype");
 }
 

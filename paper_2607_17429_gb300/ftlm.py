@@ -64,6 +64,11 @@ _SIGS = {
     "ftlm_lanczos": [_P, _I, _I, _I, _U64, _U64, _I, _P, _P, _P, _P],
     "ftlm_ritz": [_I, _I, _P, _P, _P, _P, _P, _P],
     "ftlm_thermo": [_I, _P, _I, _P, ctypes.c_double, _P, _P, _P, _P, _P, _P],
+    "ftlm_build_multiblock": [_P, _I, _P, _P, _P],
+    "ftlm_multiblock_info": [_P, _P, _P, _P],
+    "ftlm_multiblock_block": [_P, _I, _P],
+    "ftlm_hv_multi": [_P, _I, _I, _P, _P, _P],
+    "ftlm_lanczos_multi": [_P, _I, _I, _I, _U64, _P, _I, _P, _P, _P, _P],
     "ftlm_thermo_noalloc": [_I, _I, _P, _P, _P, _P, _P, _I, _P, ctypes.c_double, _P, _P, _P],
     "ftlm_profile_enable": [_I],
     "ftlm_profile_reset": [],
@@ -73,13 +78,14 @@ for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = ctypes.c_int
-for _name in ("ftlm_group_free", "ftlm_sector_free", "ftlm_basis_free"):
+for _name in ("ftlm_group_free", "ftlm_sector_free", "ftlm_basis_free", "ftlm_multiblock_free"):
     getattr(_lib, _name).argtypes = [_P]
     getattr(_lib, _name).restype = None
 _lib.ftlm_last_error.restype = ctypes.c_char_p
 _lib.ftlm_last_error.argtypes = []
 
-EXPORTED = sorted(list(_SIGS) + ["ftlm_group_free", "ftlm_sector_free", "ftlm_basis_free", "ftlm_last_error"])
+EXPORTED = sorted(list(_SIGS) + ["ftlm_group_free", "ftlm_sector_free", "ftlm_basis_free", "ftlm_multiblock_free",
+                                  "ftlm_last_error"])
 
 
 def _check(st):
@@ -260,6 +266,68 @@ def ftlm_basis_export(b: Basis):
 
 def ftlm_basis_check(b: Basis, stream=None) -> None:
     _check(_lib.ftlm_basis_check(b.handle, _stream(stream)))
+
+
+class MultiBlock:
+    def __init__(self, handle, sector):
+        self._h = handle
+        self._sector = sector
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.ftlm_multiblock_free(self._h)
+            self._h = None
+
+
+class _Borrowed:
+    def __init__(self, handle, owner):
+        self.handle = handle
+        self._owner = owner
+
+
+def ftlm_build_multiblock(s: Sector, irreps, stream=None) -> MultiBlock:
+    ir = np.ascontiguousarray(irreps, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(_lib.ftlm_build_multiblock(s.handle, len(ir), _ptr(ir), _stream(stream), ctypes.byref(h)))
+    return MultiBlock(h.value, s)
+
+
+def ftlm_multiblock_info(mb: MultiBlock) -> dict:
+    n = _I()
+    _check(_lib.ftlm_multiblock_info(mb.handle, ctypes.byref(n), None, None))
+    dims = np.zeros(n.value, dtype=np.uint64)
+    nb = ctypes.c_size_t()
+    _check(_lib.ftlm_multiblock_info(mb.handle, None, _ptr(dims), ctypes.byref(nb)))
+    return dict(n_blocks=n.value, dims=[int(d) for d in dims], device_bytes=nb.value)
+
+
+def ftlm_multiblock_block(mb: MultiBlock, k: int):
+    h = ctypes.c_void_p()
+    _check(_lib.ftlm_multiblock_block(mb.handle, k, ctypes.byref(h)))
+    return _Borrowed(h.value, mb)
+
+
+def ftlm_hv_multi(mb: MultiBlock, dtype: int, B: int, xs, ys, stream=None) -> None:
+    n = len(xs)
+    xa = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    ya = (ctypes.c_void_p * n)(*[_ptr(y) for y in ys])
+    _check(_lib.ftlm_hv_multi(mb.handle, dtype, B, xa, ya, _stream(stream)))
+
+
+def ftlm_lanczos_multi(mb: MultiBlock, dtype: int, R: int, n_steps: int, seed: int, block_ids, rng: int = GAUSS,
+                       stream=None):
+    K = ftlm_multiblock_info(mb)["n_blocks"]
+    ids = np.ascontiguousarray(block_ids, dtype=np.uint64)
+    alpha = np.zeros((K, R, n_steps))
+    beta = np.zeros((K, R, n_steps))
+    steps = np.zeros((K, R), dtype=np.int32)
+    _check(_lib.ftlm_lanczos_multi(mb.handle, dtype, R, n_steps, seed, _ptr(ids), rng, _stream(stream), _ptr(alpha),
+                                   _ptr(beta), _ptr(steps)))
+    return alpha, beta, steps
 
 
 # ---------------------------------------------------------------- H·v, Lanczos, thermo

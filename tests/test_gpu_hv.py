@@ -153,3 +153,55 @@ def test_hv_icosidodecahedron_m0_sampled_rows(dtype_name):
                 continue
             got = Y[int(off[p]):int(off[p]) + int(ng[p])]
             assert np.abs(got - yr).max() <= tol * scale
+
+
+@pytest.mark.parametrize("name,two_s,two_M,B", [("icosahedron", 1, 0, 8), ("icosahedron", 1, 2, 1),
+                                                ("icosahedron", 3, 4, 13), ("cuboctahedron", 2, 2, 8),
+                                                ("square:4x4", 1, 0, 4)])
+def test_hv_multi_matches_single_and_oracle(name, two_s, two_M, B):
+    """One multi-block launch over all irreps = per-block H·v = oracle (FP64), and FP32 close."""
+    torch = torch_cuda()
+    F = ftlm()
+    g = product_group(name)
+    og = oracle_group(name)
+    c = cluster(name)
+    sec = F.ftlm_build_sector(g, two_s, two_M)
+    irreps = [i for i, ir in enumerate(og.irreps) if ir.dim <= 5][:16]
+    mb = F.ftlm_build_multiblock(sec, irreps)
+    dims = F.ftlm_multiblock_info(mb)["dims"]
+    osec = _oracle_sector(name, two_s, two_M)
+    for dtype, tdt, tol in ((F.F64, torch.float64, 1e-13), (F.F32, torch.float32, 3e-6)):
+        xs, ys, refs = [], [], []
+        for k, ir in enumerate(irreps):
+            x = rand_block_vectors(max(dims[k], 1), B, seed=7 * k + B)[: dims[k]]
+            xs.append(torch.from_numpy(np.ascontiguousarray(x)).to("cuda", tdt) if dims[k] else
+                      torch.zeros(1, dtype=tdt, device="cuda"))
+            ys.append(torch.full_like(xs[-1], float("nan")))
+            refs.append(BlockBasis(osec, ir).with_hamiltonian(c.bonds).hv(x) if dims[k] else None)
+        F.ftlm_hv_multi(mb, dtype, B, xs, ys)
+        for k in range(len(irreps)):
+            if dims[k] == 0:
+                continue
+            blk = F.ftlm_multiblock_block(mb, k)
+            y1 = torch.empty_like(xs[k])
+            F.ftlm_hv(blk, dtype, B, xs[k], y1)
+            F.ftlm_basis_check(blk)
+            scale = np.abs(refs[k]).max() + 1e-300
+            assert np.abs(ys[k].double().cpu().numpy() - refs[k]).max() <= tol * scale
+            assert np.abs(ys[k].double().cpu().numpy() - y1.double().cpu().numpy()).max() <= tol * scale
+
+
+def test_lanczos_multi_matches_single():
+    F = ftlm()
+    g = product_group("icosahedron")
+    sec = F.ftlm_build_sector(g, 3, 2)
+    irreps = list(range(10))
+    mb = F.ftlm_build_multiblock(sec, irreps)
+    ids = [100 + k for k in irreps]
+    a, b, st = F.ftlm_lanczos_multi(mb, F.F64, 5, 15, 9, ids)
+    for k in irreps:
+        blk = F.ftlm_multiblock_block(mb, k)
+        a1, b1, s1 = F.ftlm_lanczos(blk, F.F64, 5, 15, 9, ids[k])
+        assert np.array_equal(st[k], s1)
+        assert np.allclose(a[k], a1, rtol=1e-10, atol=1e-10)
+        assert np.allclose(b[k], b1, rtol=1e-10, atol=1e-10)
