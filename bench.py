@@ -238,8 +238,11 @@ def _traffic_record(kernel, dtype_name):
     """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
     import hashlib
 
-    src = os.path.join(ROOT, "paper_2607_17429_gb300", "csrc", "hv_multi_impl.cuh")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in ("hv_kernel.cuh", "contract.cuh"):
+        with open(os.path.join(ROOT, "paper_2607_17429_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    sha = h.hexdigest()[:16]
     path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
     try:
         for ln in open(path):
@@ -270,7 +273,7 @@ def hv_roofline(prof, dtype_name, flips, G, sum_d2, B, rows, n_reps, K, esize):
     byt = 2 * rows * esize + n_reps * (8 + 2 + 4 * K)
     hbm_peak = float(pk["hbm_gbs"]) * 1e9
     alu = {"bound": "alu", "achieved": ops / t / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
-           "frac": ops / t / alu_peak, "traffic": _traffic_record("hv_multi_kernel", dtype_name),
+           "frac": ops / t / alu_peak, "traffic": _traffic_record("hv_kernel", dtype_name),
            "algorithmic_per_launch": ops, "peak_source": "derived: 152 SMs x 128 lanes x max SM clock"}
     hbm = {"bound": "hbm", "achieved": byt / t / 1e9, "peak": hbm_peak / 1e9, "unit": "GB/s",
            "frac": byt / t / hbm_peak, "traffic": alu["traffic"], "algorithmic_per_launch": byt,
