@@ -320,6 +320,36 @@ ftlm_status ftlm_profile_enable(int on);
 ftlm_status ftlm_profile_reset(void);
 ftlm_status ftlm_profile_get(ftlm_profile *out);
 
+/*
+ * Roofline denominators measured on the current device (no counterpart in the
+ * paper; it reports hardware counters only).  Each probe runs a fixed grid of
+ * 4 CTAs per SM, once to warm up and once timed with CUDA events on
+ * cuda_stream, and writes the sustained rate to *rate:
+ *   FTLM_PEAK_LOP3 / _MIN_U32 / _ADD_U64  integer lane-operations per second
+ *   FTLM_PEAK_FFMA32 / _DFMA64            fused multiply-adds per second (lanes)
+ *   FTLM_PEAK_LDS32                       conflict-free 32-bit shared loads per second
+ *   FTLM_PEAK_GATHER                      bytes per second of random aligned segments
+ *                                         of seg bytes (a multiple of 16) read from a
+ *                                         device buffer of span bytes (the segments
+ *                                         drawn from the first 2^floor(log2(span/seg)))
+ *   FTLM_PEAK_STREAM                      bytes per second (read + write) of a copy
+ *                                         of span bytes
+ * span and seg are ignored by the arithmetic probes.  The gather and stream
+ * probes allocate their buffers (span <= 64 GiB) and free them before
+ * returning.  Synchronises cuda_stream.
+ */
+enum {
+    FTLM_PEAK_LOP3 = 0,
+    FTLM_PEAK_MIN_U32 = 1,
+    FTLM_PEAK_ADD_U64 = 2,
+    FTLM_PEAK_FFMA32 = 3,
+    FTLM_PEAK_DFMA64 = 4,
+    FTLM_PEAK_LDS32 = 5,
+    FTLM_PEAK_GATHER = 6,
+    FTLM_PEAK_STREAM = 7
+};
+ftlm_status ftlm_peak_probe(int kind, uint64_t span, int seg, void *cuda_stream, double *rate);
+
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char *ftlm_last_error(void);
 

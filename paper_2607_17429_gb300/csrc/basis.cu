@@ -234,15 +234,15 @@ ftlm_status build_search_tables(ftlm_sector *s) {
     FTLM_CUDA(cudaMemcpy(s->d_bonds, bnd.data(), bnd.size(), cudaMemcpyHostToDevice));
     auto pi = [&](int g, int k) { return P[(size_t)(g < G ? g : 0) * N + k]; };  // padded with the identity
     if (s->half) {
-        s->n_chunks = (N + 1) / 2;  // 2-site chunks: 4 values each
-        std::vector<uint32_t> lut((size_t)s->n_chunks * 4 * kMaxG, 0);
+        s->n_chunks = (N + 3) / 4;
+        std::vector<uint32_t> lut((size_t)s->n_chunks * 16 * kMaxG, 0);
         for (int c = 0; c < s->n_chunks; ++c)
-            for (int v = 0; v < 4; ++v)
+            for (int v = 0; v < 16; ++v)
                 for (int g = 0; g < kMaxG; ++g) {
                     uint32_t img = 0;
-                    for (int t = 0; t < 2; ++t)
-                        if (((v >> t) & 1) && 2 * c + t < N) img |= 1u << pi(g, 2 * c + t);
-                    lut[((size_t)c * 4 + v) * kMaxG + g] = img;
+                    for (int t = 0; t < 4; ++t)
+                        if (((v >> t) & 1) && 4 * c + t < N) img |= 1u << pi(g, 4 * c + t);
+                    lut[((size_t)c * 16 + v) * kMaxG + g] = img;
                 }
         std::vector<uint32_t> dt((size_t)nb * kMaxG);
         for (int e = 0; e < nb; ++e)

@@ -4,7 +4,7 @@
 // One warp per output representative r (persistent grid-stride walk over the
 // sorted table):
 //  1. images I_g = U(g) r for the lane's group elements g = lane + 32c, from a
-//     shared table (s = 1/2: image of every 2-site chunk; general s: the bit
+//     shared table (s = 1/2: image of every 4-site nibble; general s: the bit
 //     position of every site after g);
 //  2. lanes over bonds: diagonal term J sum m_i m_j (Eq. 16) and the admissible
 //     ladder flips (Eq. 3), compacted with ballots;
@@ -16,21 +16,13 @@
 //     search in the sorted table; the flip record (index, stabilizer id, g*,
 //     c_a) goes to the warp's shared-memory slot;
 //  5. per block k with n_k(r) > 0 (steps 1-4 are irrep independent and run
-//     once): the x rows of every flip's r' are staged into the warp's shared
-//     buffer by TMA bulk copies (one cp.async.bulk per flip, completion on an
-//     mbarrier, all flips of a chunk in flight together) -- or read directly
-//     when the rows are not 16-byte multiples -- and lanes = (flip group,
-//     right-hand side) accumulate
+//     once): lanes = (flip group, right-hand side) accumulate
 //       z += c_a sqrt|Stab r'| rho_k(g*)^T V_k(r') x_k(r')   (rho(g_e) = rho(g*)^T)
-//     with the contraction specialised on d_k; then
+//     with the contraction specialised on d_k, then
 //       y_k(r) = V_k(r)^T z / sqrt|Stab r| + diag x_k(r).
-// Row offsets are [n_reps][K].  FP32 keeps the rho tables in shared memory;
-// FP64 reads them through the read-only cache.  Every mbarrier wait is bounded
-// (about two seconds); on expiry the kernel sets an error bit and returns.
+// Row offsets are [n_reps][K] (one record per lookup).  FP32 keeps the rho
+// tables in shared memory; FP64 reads them through the read-only cache.
 #pragma once
-
-#include <stdlib.h>
-#include <string.h>
 
 #include <type_traits>
 
@@ -39,13 +31,14 @@
 namespace ftlm {
 
 constexpr int kMaxK = 16;
-constexpr int kHvThreads = 512;
-constexpr int kStageBytes = 5120;  // per-warp TMA staging buffer
-constexpr int kErrMissing = 1, kErrTimeout = 8;
 
-// flips of one representative: one per bond (s = 1/2) or up to two; multiple of 4
-__host__ __device__ inline int hv_max_flips(bool half, int n_bonds) {
-    return ((half ? n_bonds : 2 * n_bonds) + 3) & ~3;
+template <typename VT>
+__host__ __device__ constexpr int hv_threads() {
+    return sizeof(VT) == 8 ? 512 : 1024;
+}
+template <bool HALF>
+__host__ __device__ constexpr int hv_max_flips() {
+    return HALF ? 64 : 128;  // one flip per bond (s = 1/2) or two
 }
 
 template <typename VT>
@@ -95,55 +88,15 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int n) {
     return pos;
 }
 
-// ---------------------------------------------------------------- TMA bulk copy + mbarrier (inline PTX)
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-// try_wait with a suspend-time hint (ns): the warp sleeps in hardware until the
-// phase completes or the hint expires, instead of spinning on issue slots.
-__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity), "r"(1000000u)
-        : "memory");
-    return ok;
-}
-// Warp-uniform bounded wait for the phase with the given parity (about 2^32 cycles).
-__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    for (;;) {
-        const uint32_t ok = mbar_try_wait(bar, parity);
-        if (__all_sync(kFull, ok)) return true;
-        const long long dt = __shfl_sync(kFull, clock64() - t0, 0);
-        if (dt > (1ll << 32)) return false;
-    }
-}
-
 template <typename VT>
 struct HvLayout {
-    size_t o_dtab, o_rho, o_bond, o_flip, o_bar, o_stage, total;
+    size_t o_dtab, o_rho, o_bond, o_flip, total;
 };
 
 template <typename VT, bool HALF>
-__host__ __device__ inline HvLayout<VT> hv_layout(int n_chunks, int n_bonds, int rho_total, int warps, bool tma) {
+__host__ __device__ inline HvLayout<VT> hv_layout(int n_chunks, int n_bonds, int rho_total, int warps) {
     HvLayout<VT> L;
-    size_t o = HALF ? (size_t)n_chunks * 4 * kMaxG * 4 : (size_t)kMaxG * 64;
+    size_t o = HALF ? (size_t)n_chunks * 16 * kMaxG * 4 : (size_t)kMaxG * 64;
     o = (o + 15) & ~(size_t)15;
     L.o_dtab = o;
     o += (size_t)n_bonds * kMaxG * (HALF ? 4 : 8);
@@ -154,162 +107,45 @@ __host__ __device__ inline HvLayout<VT> hv_layout(int n_chunks, int n_bonds, int
     L.o_bond = o;
     o += (size_t)n_bonds * 2;
     o = (o + 15) & ~(size_t)15;
-    L.o_flip = o;  // per warp: idx[MAXF], sg[MAXF] (u32), c[MAXF] (VT; s = 1/2 uses the constant J/2)
-    o += (size_t)warps * hv_max_flips(HALF, n_bonds) * (8 + (HALF ? 0 : sizeof(VT)));
-    o = (o + 15) & ~(size_t)15;
-    L.o_bar = o;  // per warp: one mbarrier
-    o += (size_t)warps * 8;
-    o = (o + 127) & ~(size_t)127;
-    L.o_stage = o;  // per warp: staging buffer
-    if (tma) o += (size_t)warps * kStageBytes;
+    L.o_flip = o;
+    o += (size_t)warps * hv_max_flips<HALF>() * (8 + sizeof(VT));
     L.total = o;
     return L;
 }
 
-struct FlipRecs {
-    const uint32_t *idx, *sg;
-};
-
-// coefficient c_a of flip f: stored per flip, or the constant J/2 for s = 1/2 (c == nullptr)
-template <typename VT>
-__device__ __forceinline__ VT flip_coef(const VT *c, VT c_const, int f) {
-    return c ? c[f] : c_const;
-}
-
-// Block k, direct gathers (rows not 16-byte multiples).
+// Block k's pass over the flips of one representative (steps 5 and 6).
 template <typename VT, int BT, int D>
-__device__ __forceinline__ void block_pass_direct(const HvArgs<VT> &a, int k, int nf, FlipRecs fr, const VT *f_c,
-                                                  VT c_const, const VT *rk, int lane, VT *z) {
+__device__ __forceinline__ void block_pass(const HvArgs<VT> &a, int k, uint64_t rep, int sid, int n_rk, int nf,
+                                           VT diag, const uint32_t *f_idx, const uint32_t *f_sg, const VT *f_c,
+                                           const VT *rk, int lane) {
     constexpr int P = 32 / BT;
     constexpr int RP = rho_row(D);
     const int b = lane % BT, fg = lane / BT;
     const int B = a.B, K = a.K;
     const VT *xk = a.x[k];
     const VT *Vk = a.V[k];
+    VT z[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) z[i] = (VT)0;
     for (int t = 0; t < nf; t += P) {
         const int f = t + fg;
         if (f < nf && b < B) {
-            const uint32_t sg = fr.sg[f];
+            const uint32_t sg = f_sg[f];
             const int sid_j = (int)(sg >> 8), g_j = (int)(sg & 255u);
             const int n_j = __ldg(a.ntab + k * a.n_sid + sid_j);
             if (n_j > 0) {
-                const uint64_t off_j = __ldg(a.off + (uint64_t)fr.idx[f] * K + k);
-                const VT cf = flip_coef(f_c, c_const, f) * __ldg(a.sqrtS + sid_j);
+                const uint64_t off_j = __ldg(a.off + (uint64_t)f_idx[f] * K + k);
+                const VT cf = f_c[f] * __ldg(a.sqrtS + sid_j);
                 contract_flip<VT, D>(rk + g_j * D * RP, xk + off_j * B + b, B, sid_j, n_j, Vk + (size_t)sid_j * D * D,
                                      cf, z);
             }
         }
-    }
-}
-
-// Block k, gathers staged by TMA bulk copies: FC flips per chunk, one copy per flip.
-// Returns false if an mbarrier wait expired.
-template <typename VT, int BT, int D>
-__device__ __forceinline__ bool block_pass_tma(const HvArgs<VT> &a, int k, int nf, FlipRecs fr, const VT *f_c,
-                                               VT c_const, const VT *rk, int lane, VT *z, VT *stage, uint32_t bar,
-                                               uint32_t &phase) {
-    constexpr int P = 32 / BT;
-    constexpr int RP = rho_row(D);
-    constexpr int ROW = BT * (int)sizeof(VT);                      // bytes of one row (B == BT here)
-    constexpr int FC = kStageBytes / (5 * ROW) < 32 ? kStageBytes / (5 * ROW) : 32;  // flips per chunk
-    const int b = lane % BT, fg = lane / BT;
-    const int K = a.K;
-    const VT *xk = a.x[k];
-    const VT *Vk = a.V[k];
-    const uint32_t stage_s = smem_addr(stage);
-    for (int fb = 0; fb < nf; fb += FC) {
-        const int nc = min(FC, nf - fb);
-        // per-flip copy size and destination (exclusive prefix over the chunk)
-        uint32_t bytes = 0;
-        uint64_t off_j = 0;
-        int n_j = 0;
-        if (lane < nc) {
-            const uint32_t sg = fr.sg[fb + lane];
-            n_j = __ldg(a.ntab + k * a.n_sid + (int)(sg >> 8));
-            if (n_j > 0) {
-                off_j = __ldg(a.off + (uint64_t)fr.idx[fb + lane] * K + k);
-                bytes = (uint32_t)(n_j * ROW);
-            }
-        }
-        uint32_t pre = bytes;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(kFull, pre, o);
-            if (lane >= o) pre += v;
-        }
-        const uint32_t total = __shfl_sync(kFull, pre, 31);
-        pre -= bytes;
-        fence_proxy_async();  // earlier generic reads of the buffer before the async writes
-        __syncwarp();
-        if (lane == 0) mbar_arrive_expect_tx(bar, total);
-        __syncwarp();
-        if (bytes) bulk_g2s(stage_s + pre, xk + off_j * BT, bytes, bar);
-        if (!mbar_wait_warp(bar, phase)) return false;
-        phase ^= 1u;
-        for (int t = 0; t < nc; t += P) {
-            const int jl = t + fg;
-            const int srcl = jl < nc ? jl : 0;
-            const uint32_t pj = __shfl_sync(kFull, pre, srcl);
-            const int nj = __shfl_sync(kFull, n_j, srcl);
-            if (jl < nc && nj > 0) {
-                const uint32_t sg = fr.sg[fb + jl];
-                const int sid_j = (int)(sg >> 8), g_j = (int)(sg & 255u);
-                const VT *xs = stage + pj / sizeof(VT) + b;
-                VT u[D];
-                if (sid_j == 0) {
-#pragma unroll
-                    for (int i = 0; i < D; ++i) u[i] = xs[i * BT];
-                } else {
-                    const VT *Vt = Vk + (size_t)sid_j * D * D;
-#pragma unroll
-                    for (int i = 0; i < D; ++i) u[i] = (VT)0;
-                    for (int kp = 0; kp < nj; ++kp) {
-                        const VT xv = xs[kp * BT];
-#pragma unroll
-                        for (int i = 0; i < D; ++i) u[i] += __ldg(Vt + i * D + kp) * xv;
-                    }
-                }
-                const VT cf = flip_coef(f_c, c_const, fb + jl) * __ldg(a.sqrtS + sid_j);
-                const VT *R = rk + g_j * D * RP;
-#pragma unroll
-                for (int be = 0; be < D; ++be) {
-                    VT row[RP];
-                    load_row<VT, RP>(R + be * RP, row);
-                    VT acc = row[0] * u[0];
-#pragma unroll
-                    for (int ga = 1; ga < D; ++ga) acc += row[ga] * u[ga];
-                    z[be] += cf * acc;
-                }
-            }
-        }
-        __syncwarp();
-    }
-    return true;
-}
-
-// Block k: contraction over all flips, reduction over flip groups, output rows.
-template <typename VT, int BT, int D, bool TMA>
-__device__ __forceinline__ bool block_pass(const HvArgs<VT> &a, int k, uint64_t rep, int sid, int n_rk, int nf,
-                                           VT diag, FlipRecs fr, const VT *f_c, VT c_const, const VT *rk, int lane,
-                                           VT *stage, uint32_t bar, uint32_t &phase) {
-    constexpr int P = 32 / BT;
-    const int b = lane % BT, fg = lane / BT;
-    const int B = a.B, K = a.K;
-    VT z[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) z[i] = (VT)0;
-    if (TMA) {
-        if (!block_pass_tma<VT, BT, D>(a, k, nf, fr, f_c, c_const, rk, lane, z, stage, bar, phase)) return false;
-    } else {
-        block_pass_direct<VT, BT, D>(a, k, nf, fr, f_c, c_const, rk, lane, z);
     }
 #pragma unroll
     for (int w = BT; w < 32; w <<= 1)
 #pragma unroll
         for (int i = 0; i < D; ++i) z[i] += __shfl_xor_sync(kFull, z[i], w);
     if (b < B) {
-        const VT *xk = a.x[k];
-        const VT *Vk = a.V[k];
         const VT inv_sq = (VT)1 / __ldg(a.sqrtS + sid);
         const VT *Vr = Vk + (size_t)sid * D * D;
         const uint64_t off_r = __ldg(a.off + rep * K + k);
@@ -322,20 +158,17 @@ __device__ __forceinline__ bool block_pass(const HvArgs<VT> &a, int k, uint64_t 
             yk[row] = val * inv_sq + diag * __ldg(xk + row);
         }
     }
-    return true;
 }
 
-template <typename VT, int BT, int GPL, bool HALF, bool TMA>
-__global__ void __launch_bounds__(kHvThreads, 1) hv_kernel(HvArgs<VT> a) {
+template <typename VT, int BT, int GPL, bool HALF>
+__global__ void __launch_bounds__(hv_threads<VT>(), 1) hv_kernel(HvArgs<VT> a) {
     using LT = typename std::conditional<HALF, uint32_t, uint64_t>::type;
-    const int MAXF = hv_max_flips(HALF, a.n_bonds);
-    extern __shared__ __align__(128) uint8_t smem[];
+    constexpr int MAXF = hv_max_flips<HALF>();
+    extern __shared__ __align__(16) uint8_t smem[];
     const int warps = blockDim.x >> 5;
-    const HvLayout<VT> L = hv_layout<VT, HALF>(a.n_chunks, a.n_bonds, a.rho_total, warps, TMA);
-    const int wid = threadIdx.x >> 5;
-    const int lane = threadIdx.x & 31;
+    const HvLayout<VT> L = hv_layout<VT, HALF>(a.n_chunks, a.n_bonds, a.rho_total, warps);
     {
-        const size_t n_tab = HALF ? (size_t)a.n_chunks * 4 * kMaxG * 4 : (size_t)kMaxG * 64;
+        const size_t n_tab = HALF ? (size_t)a.n_chunks * 16 * kMaxG * 4 : (size_t)kMaxG * 64;
         const uint4 *src0 = reinterpret_cast<const uint4 *>(HALF ? (const void *)a.lut : (const void *)a.pos);
         for (size_t i = threadIdx.x; i < n_tab / 16; i += blockDim.x) reinterpret_cast<uint4 *>(smem)[i] = src0[i];
         const size_t n_dt = (size_t)a.n_bonds * kMaxG * (HALF ? 4 : 8);
@@ -348,11 +181,6 @@ __global__ void __launch_bounds__(kHvThreads, 1) hv_kernel(HvArgs<VT> a) {
                 reinterpret_cast<uint4 *>(smem + L.o_rho)[i] = src2[i];
         }
         for (int i = threadIdx.x; i < 2 * a.n_bonds; i += blockDim.x) smem[L.o_bond + i] = a.bonds[i];
-        if (TMA && lane == 0) mbar_init(smem_addr(smem + L.o_bar + 8 * wid), 1);
-        if (TMA) {
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            fence_proxy_async();
-        }
     }
     __syncthreads();
     const uint32_t *s_lut = reinterpret_cast<const uint32_t *>(smem);
@@ -360,14 +188,12 @@ __global__ void __launch_bounds__(kHvThreads, 1) hv_kernel(HvArgs<VT> a) {
     const LT *s_dtab = reinterpret_cast<const LT *>(smem + L.o_dtab);
     const VT *rho_base = sizeof(VT) == 4 ? reinterpret_cast<const VT *>(smem + L.o_rho) : a.rhoT;
     const uint8_t *s_bond = smem + L.o_bond;
+    const int wid = threadIdx.x >> 5;
     uint32_t *f_idx = reinterpret_cast<uint32_t *>(smem + L.o_flip) + (size_t)wid * MAXF * 2;
     uint32_t *f_sg = f_idx + MAXF;
-    VT *f_c = HALF ? nullptr
-                   : reinterpret_cast<VT *>(smem + L.o_flip + (size_t)warps * MAXF * 8) + (size_t)wid * MAXF;
-    const uint32_t bar = smem_addr(smem + L.o_bar + 8 * wid);
-    VT *stage = reinterpret_cast<VT *>(smem + L.o_stage + (size_t)wid * kStageBytes);
-    uint32_t phase = 0;
+    VT *f_c = reinterpret_cast<VT *>(smem + L.o_flip + (size_t)warps * MAXF * 8) + (size_t)wid * MAXF;
 
+    const int lane = threadIdx.x & 31;
     const int K = a.K;
     const uint64_t nw = (uint64_t)gridDim.x * warps;
     const VT halfJ = a.J * (VT)0.5;
@@ -385,7 +211,7 @@ __global__ void __launch_bounds__(kHvThreads, 1) hv_kernel(HvArgs<VT> a) {
             const int g = lane + 32 * c;
             LT v = 0;
             if (HALF) {
-                for (int q = 0; q < a.n_chunks; ++q) v |= s_lut[(q * 4 + (int)((lab >> (2 * q)) & 3)) * kMaxG + g];
+                for (int q = 0; q < a.n_chunks; ++q) v |= s_lut[(q * 16 + (int)((lab >> (4 * q)) & 15)) * kMaxG + g];
             } else {
                 for (int k = 0; k < a.N; ++k) v += (LT)hv_digit(lab, k, a.bits) << s_pos[g * 64 + k];
             }
@@ -496,45 +322,38 @@ __global__ void __launch_bounds__(kHvThreads, 1) hv_kernel(HvArgs<VT> a) {
                     }
                 }
                 if (!found) {
-                    atomicOr(a.err, kErrMissing);
+                    atomicOr(a.err, 1);
                     my_c = (VT)0;
                 }
                 f_idx[base + lane] = idx;
-                f_sg[base + lane] = ((uint32_t)sid_f << 8) | (uint32_t)my_g;  // my_g < |G| always
-                if (!HALF) f_c[base + lane] = my_c;
+                f_sg[base + lane] = ((uint32_t)sid_f << 8) | (uint32_t)my_g;
+                f_c[base + lane] = my_c;
             }
         }
         __syncwarp();
 
         // 5-6. contraction and output, block by block
-        const FlipRecs fr{f_idx, f_sg};
         for (int k = 0; k < K; ++k) {
             const int n_rk = __ldg(a.ntab + k * a.n_sid + sid);
             if (n_rk == 0) continue;
             const VT *rk = rho_base + a.rho_off[k];
-            bool ok;
             switch (a.d[k]) {
-                case 1: ok = block_pass<VT, BT, 1, TMA>(a, k, rep, sid, n_rk, nf, diag, fr, f_c, halfJ, rk, lane, stage, bar, phase); break;
-                case 2: ok = block_pass<VT, BT, 2, TMA>(a, k, rep, sid, n_rk, nf, diag, fr, f_c, halfJ, rk, lane, stage, bar, phase); break;
-                case 3: ok = block_pass<VT, BT, 3, TMA>(a, k, rep, sid, n_rk, nf, diag, fr, f_c, halfJ, rk, lane, stage, bar, phase); break;
-                case 4: ok = block_pass<VT, BT, 4, TMA>(a, k, rep, sid, n_rk, nf, diag, fr, f_c, halfJ, rk, lane, stage, bar, phase); break;
-                default: ok = block_pass<VT, BT, 5, TMA>(a, k, rep, sid, n_rk, nf, diag, fr, f_c, halfJ, rk, lane, stage, bar, phase); break;
-            }
-            if (!ok) {  // an mbarrier wait expired: report, let copies in flight land (bounded), stop
-                if (lane == 0) atomicOr(a.err, kErrTimeout);
-                mbar_wait_warp(bar, phase);
-                return;
+                case 1: block_pass<VT, BT, 1>(a, k, rep, sid, n_rk, nf, diag, f_idx, f_sg, f_c, rk, lane); break;
+                case 2: block_pass<VT, BT, 2>(a, k, rep, sid, n_rk, nf, diag, f_idx, f_sg, f_c, rk, lane); break;
+                case 3: block_pass<VT, BT, 3>(a, k, rep, sid, n_rk, nf, diag, f_idx, f_sg, f_c, rk, lane); break;
+                case 4: block_pass<VT, BT, 4>(a, k, rep, sid, n_rk, nf, diag, f_idx, f_sg, f_c, rk, lane); break;
+                default: block_pass<VT, BT, 5>(a, k, rep, sid, n_rk, nf, diag, f_idx, f_sg, f_c, rk, lane); break;
             }
         }
         __syncwarp();
     }
 }
 
-template <typename VT, int BT, int GPL, bool HALF, bool TMA>
+template <typename VT, int BT, int GPL, bool HALF>
 ftlm_status launch_hv_t(const HvArgs<VT> &a, cudaStream_t stream) {
-    auto kern = hv_kernel<VT, BT, GPL, HALF, TMA>;
-    const int threads = kHvThreads;
-    const size_t smem = hv_layout<VT, HALF>(a.n_chunks, a.n_bonds, a.rho_total, threads / 32, TMA).total;
+    auto kern = hv_kernel<VT, BT, GPL, HALF>;
+    constexpr int threads = hv_threads<VT>();
+    const size_t smem = hv_layout<VT, HALF>(a.n_chunks, a.n_bonds, a.rho_total, threads / 32).total;
     FTLM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     FTLM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -554,39 +373,14 @@ ftlm_status launch_hv_t(const HvArgs<VT> &a, cudaStream_t stream) {
     return FTLM_OK;
 }
 
-// TMA staging needs rows (B values) of a 16-byte multiple and 16-byte aligned vectors.
-// FTLM_HV_GATHER=direct disables the TMA staging (tuning knob; default: TMA when possible).
-inline bool hv_tma_allowed() {
-    static const int allowed = [] {
-        const char *v = getenv("FTLM_HV_GATHER");
-        return (v && strcmp(v, "direct") == 0) ? 0 : 1;
-    }();
-    return allowed != 0;
-}
-
-template <typename VT, int BT, int GPL, bool HALF>
-ftlm_status launch_hv_tma_or_direct(const HvArgs<VT> &a, cudaStream_t stream) {
-    bool tma = hv_tma_allowed() && a.B == BT && (BT * sizeof(VT)) % 16 == 0;
-    for (int k = 0; k < a.K && tma; ++k) tma = ((uintptr_t)a.x[k] % 16) == 0;
-    int dev = 0, max_smem = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (hv_layout<VT, HALF>(a.n_chunks, a.n_bonds, a.rho_total, kHvThreads / 32, true).total > (size_t)max_smem)
-        tma = false;
-    if constexpr ((BT * sizeof(VT)) % 16 == 0) {
-        if (tma) return launch_hv_t<VT, BT, GPL, HALF, true>(a, stream);
-    }
-    return launch_hv_t<VT, BT, GPL, HALF, false>(a, stream);
-}
-
 template <typename VT, int GPL, bool HALF>
 ftlm_status launch_hv_b(const HvArgs<VT> &a, cudaStream_t stream) {
-    if (a.B <= 1) return launch_hv_tma_or_direct<VT, 1, GPL, HALF>(a, stream);
-    if (a.B <= 2) return launch_hv_tma_or_direct<VT, 2, GPL, HALF>(a, stream);
-    if (a.B <= 4) return launch_hv_tma_or_direct<VT, 4, GPL, HALF>(a, stream);
-    if (a.B <= 8) return launch_hv_tma_or_direct<VT, 8, GPL, HALF>(a, stream);
-    if (a.B <= 16) return launch_hv_tma_or_direct<VT, 16, GPL, HALF>(a, stream);
-    return launch_hv_tma_or_direct<VT, 32, GPL, HALF>(a, stream);
+    if (a.B <= 1) return launch_hv_t<VT, 1, GPL, HALF>(a, stream);
+    if (a.B <= 2) return launch_hv_t<VT, 2, GPL, HALF>(a, stream);
+    if (a.B <= 4) return launch_hv_t<VT, 4, GPL, HALF>(a, stream);
+    if (a.B <= 8) return launch_hv_t<VT, 8, GPL, HALF>(a, stream);
+    if (a.B <= 16) return launch_hv_t<VT, 16, GPL, HALF>(a, stream);
+    return launch_hv_t<VT, 32, GPL, HALF>(a, stream);
 }
 
 template <typename VT>

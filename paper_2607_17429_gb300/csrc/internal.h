@@ -69,7 +69,7 @@ struct ftlm_sector {
     int bucket_shift = 0;
     uint64_t n_buckets = 0;
     // H·v search tables
-    uint32_t *d_lut = nullptr;   // s = 1/2: [nchunk][4][kMaxG] image of a 2-site chunk under g
+    uint32_t *d_lut = nullptr;   // s = 1/2: [nchunk][16][kMaxG] image of a 4-site nibble under g
     int n_chunks = 0;
     uint8_t *d_pos = nullptr;    // general s: [kMaxG][64] bit position of site k's field after g
     void *d_dtab = nullptr;      // [n_bonds][kMaxG] u32 XOR masks (s = 1/2) or int64 deltas (general)

@@ -70,6 +70,7 @@ _SIGS = {
     "ftlm_hv_multi": [_P, _I, _I, _P, _P, _P],
     "ftlm_lanczos_multi": [_P, _I, _I, _I, _U64, _P, _I, _P, _P, _P, _P],
     "ftlm_thermo_noalloc": [_I, _I, _P, _P, _P, _P, _P, _I, _P, ctypes.c_double, _P, _P, _P],
+    "ftlm_peak_probe": [_I, _U64, _I, _P, _P],
     "ftlm_profile_enable": [_I],
     "ftlm_profile_reset": [],
     "ftlm_profile_get": [_P],
@@ -385,6 +386,16 @@ def ftlm_thermo_noalloc(n_chains, ld, m, alpha, beta, weight, msq, n_T, T, g, ou
 
 
 # ---------------------------------------------------------------- profiling
+
+PEAK_LOP3, PEAK_MIN_U32, PEAK_ADD_U64, PEAK_FFMA32, PEAK_DFMA64, PEAK_LDS32, PEAK_GATHER, PEAK_STREAM = range(8)
+
+
+def ftlm_peak_probe(kind: int, span: int = 0, seg: int = 0, stream=None) -> float:
+    """Measured rate of one probe (lane-ops/s, FMAs/s, loads/s or bytes/s; see include/ftlm.h)."""
+    r = ctypes.c_double()
+    _check(_lib.ftlm_peak_probe(int(kind), int(span), int(seg), _stream(stream), ctypes.byref(r)))
+    return r.value
+
 
 
 def ftlm_profile_enable(on: bool = True) -> None:

@@ -145,3 +145,37 @@ def test_dimer_spectrum_closed_form():
             S = twoS / 2
             ref += [0.5 * (S * (S + 1) - 2 * s * (s + 1))] * int(2 * S + 1)
         assert np.allclose(evs, np.sort(ref), atol=1e-12)
+
+
+@pytest.mark.parametrize("name,two_s,two_M", CASES)
+def test_hv_rows_by_label_matches_dense_checked_block_hv(name, two_s, two_M):
+    """The table-free, label-keyed oracle rows (Eqs. 15-16 from each label alone) equal the rows of the
+    dense-checked BlockBasis.hv on the same label-keyed input, for every irrep of every CASES sector."""
+    from oracle.basis import hv_rows_by_label
+    from workloads import label_keyed_values
+
+    c = cluster(name)
+    g = Group(c.gens, c.bonds)
+    sec = SectorBasis(g, two_s, two_M)
+    B = 3
+    checked = 0
+    for ir in range(len(g.irreps)):
+        if g.irreps[ir].rho is None:
+            continue
+        blk = BlockBasis(sec, ir).with_hamiltonian(c.bonds)
+        if blk.dim == 0:
+            continue
+        vals = label_keyed_values(sec.reps, max(1, int(blk.n.max())), B, 17 + ir)
+        X = np.concatenate([vals[i, :blk.n[i]] for i in range(sec.n_reps)])
+        Y = blk.hv(X)
+        rows = hv_rows_by_label(g, ir, c.bonds, 1.0, two_s, sec.reps,
+                                lambda lab, n, s=17 + ir: label_keyed_values([lab], n, B, s)[0])
+        scale = np.abs(Y).max() + 1e-300
+        for i, yr in enumerate(rows):
+            if blk.n[i] == 0:
+                assert yr is None
+                continue
+            assert yr.shape == (blk.n[i], B)
+            assert np.abs(yr - Y[blk.off[i]:blk.off[i + 1]]).max() <= 1e-13 * scale
+            checked += 1
+    assert checked > 0
