@@ -3,15 +3,19 @@
 
 One step = one full pass of the hot path over the workload: enumerate the M = 0
 sector on the GPU (1.55e8 states -> orbit representatives, stabilizers, lookup
-index), build the 10 irrep blocks, run R = 8 Lanczos chains of 60 steps per
-block (every step one symmetry-adapted H·v launch with B = 8 right-hand sides,
-FP64 alpha/beta), Ritz pairs and thermal sums on 200 temperatures.
+index), build the 10 irrep blocks and their packed set, run R = 8 Lanczos
+chains of 60 steps on every block (each step one packed H·v launch over all ten
+blocks with B = 8 right-hand sides, FP32 vectors, FP64 alpha/beta), Ritz pairs
+and thermal sums on 200 temperatures.
 
-value    = state-applications per second, sum over blocks of dim * R * steps
-           divided by the device time of the step (group tables resident).
+value    = state-applications per second: sum over blocks of dim * chains * steps
+           done, divided by the device time of the steps (group tables resident).
 e2e      = the same metric through the public C-ABI calls from host buffers
            (generators and bonds uploaded, alpha/beta and thermal curves read back).
-roofline = the H·v kernel (dominant launch), timed with CUDA events by the library.
+roofline = the packed H·v kernel (the dominant launch), timed with CUDA events
+           recorded inside the Lanczos graph; algorithmic bytes per launch as in
+           the kernel's roofline definition (gathers of every flipped state's
+           segment, the representative's own rows in and out, the lookups).
 """
 from __future__ import annotations
 
@@ -29,6 +33,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "icosidodecahedron s=1/2 M=0, I_h all 10 irreps, R=8 Gaussian (seed 1), 60 Lanczos steps"
+METRIC = "sym-adapted H·v Gstates/s (FTLM step: enumeration + 10 irrep blocks x 8 chains x 60 Lanczos steps + thermo)"
 CLUSTER, TWO_S, TWO_M, R, N_STEPS, SEED = "icosidodecahedron", 1, 0, 8, 60, 1
 T_GRID = 0.02 * 5000.0 ** (np.arange(200) / 199.0)
 
@@ -95,10 +100,6 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def h_g_like(info, inv_index):
-    return [i for i, d in enumerate(info["dims"])]
-
-
 def run_ours(args, rank, world):
     import torch
 
@@ -115,16 +116,16 @@ def run_ours(args, rank, world):
     c = cluster(CLUSTER)
     gens, bonds = np.ascontiguousarray(c.gens), np.ascontiguousarray(c.bonds)
     group = F.ftlm_group_init(gens, bonds)  # resident inputs for the device-timed value
-    n_ir = len(F.ftlm_group_info(group)["dims"])
     dims_g = F.ftlm_group_info(group)["dims"]
+    n_ir = len(dims_g)
+    ids = [64 * TWO_M + ir for ir in range(n_ir)]
 
     def step_multi(grp, dt):
-        """Batched form: all 10 irrep blocks through one multi-block H·v launch per Lanczos step."""
+        """Batched form: all 10 irrep blocks through one packed H·v launch per Lanczos step."""
         sec = F.ftlm_build_sector(grp, TWO_S, TWO_M, stream)
         mb = F.ftlm_build_multiblock(sec, list(range(n_ir)), stream)
         dims = F.ftlm_multiblock_info(mb)["dims"]
-        a, b, st = F.ftlm_lanczos_multi(mb, dt, R, N_STEPS, SEED, [64 * TWO_M + ir for ir in range(n_ir)], F.GAUSS,
-                                        stream)
+        a, b, st = F.ftlm_lanczos_multi(mb, dt, R, N_STEPS, SEED, ids, F.GAUSS, stream)
         blocks = [dict(two_M=TWO_M, d_gamma=int(dims_g[k]), dim=dims[k], alpha=a[k], beta=b[k], steps=st[k])
                   for k in range(n_ir)]
         states = sum(dims[k] * int(st[k].sum()) for k in range(n_ir))
@@ -137,7 +138,7 @@ def run_ours(args, rank, world):
         for ir in range(n_ir):
             blk = F.ftlm_build_block(sec, ir, stream)
             dim = F.ftlm_basis_info(blk)["dim"]
-            a, b, st = F.ftlm_lanczos(blk, dt, R, N_STEPS, SEED, 64 * TWO_M + ir, F.GAUSS, stream)
+            a, b, st = F.ftlm_lanczos(blk, dt, R, N_STEPS, SEED, ids[ir], F.GAUSS, stream)
             blocks.append(dict(two_M=TWO_M, d_gamma=int(dims_g[ir]), dim=dim, alpha=a, beta=b, steps=st))
             states += dim * int(st.sum())
         return states, F.ftlm_thermo(blocks, T_GRID, 1.0, stream)
@@ -163,6 +164,8 @@ def run_ours(args, rank, world):
             states += s
         e1.record(stream)
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         F.ftlm_profile_enable(False)
         prof = F.ftlm_profile_get()
         ms = e0.elapsed_time(e1)
@@ -178,13 +181,12 @@ def run_ours(args, rank, world):
     value = states * world / (ms_all / 1e3) / 1e9  # replicas: every rank runs the same workload
     res = {"ms": ms, "states": states, "prof": prof, "out": out, "clocks": clk.summary(), "value": value,
            "ms_all": ms_all}
-    # algorithmic counts of one multi-block H·v launch (for the roofline)
+    # algorithmic counts of one packed H·v launch (for the roofline)
     sec = F.ftlm_build_sector(group, TWO_S, TWO_M, stream)
     labels, _ = F.ftlm_sector_export(sec)
     mb = F.ftlm_build_multiblock(sec, list(range(n_ir)), stream)
-    res.update(flips=_flip_count(labels, bonds), G=F.ftlm_group_info(group)["order"],
-               sum_d2=int(sum(int(d) ** 2 for d in dims_g)), rows=sum(F.ftlm_multiblock_info(mb)["dims"]) * R,
-               n_reps=len(labels), K=n_ir)
+    res.update(flips=_flip_count(labels, bonds), n_reps=len(labels), W=int(sum(int(d) for d in dims_g)),
+               rows=F.ftlm_multiblock_packed_rows(mb), dims=F.ftlm_multiblock_info(mb)["dims"])
     del mb, sec
 
     # FP64 companions: the plain one-block-at-a-time form and the batched form (mixed vs FP64 error)
@@ -194,18 +196,17 @@ def run_ours(args, rank, world):
         for name, fn in (("plain_single_block", step_single), ("batched", step_multi)):
             ms64, st64, prof64, out64 = timed(F.F64, 1, 1, fn)
             fp64[name] = {"value": st64 / (ms64 / 1e3) / 1e9, "ms_per_step": ms64,
-                          "blocks_per_hour": 10 / (ms64 / 1e3) * 3600.0,
+                          "blocks_per_hour": n_ir / (ms64 / 1e3) * 3600.0,
                           "hv_ms_per_launch": prof64["hv_ms"] / max(1, prof64["hv_launches"]), "E0": out64[4]}
         ref = out64  # FP64 batched
         sel = T_GRID >= 0.05
         fp64["mixed_vs_fp64"] = {
             "dE0_rel": abs(out[4] - ref[4]) / abs(ref[4]),
             "max_dC_over_Cmax": float(np.abs(out[2] - ref[2])[sel].max() / ref[2].max()),
-            "max_dchi_over_chimax": (float(np.abs(out[3] - ref[3])[sel].max() / ref[3].max())
-                                     if ref[3].max() > 0 else 0.0),
-            "max_dlnZ_rel": float(np.abs((out[0] - ref[0]) / ref[0]).max())}
+            "max_dlnZ_rel": float(np.abs((out[0] - ref[0]) / ref[0]).max()),
+            "chi": "identically 0 in an M = 0-only run (chi needs M != 0 sectors)"}
         fp64["batched_mixed_over_plain_fp64_blocks_per_hour"] = (
-            (10 * args.steps / (ms / 1e3)) / (10 / (fp64["plain_single_block"]["ms_per_step"] / 1e3)))
+            (n_ir * args.steps / (ms / 1e3)) / (n_ir / (fp64["plain_single_block"]["ms_per_step"] / 1e3)))
 
     # e2e: public API from host buffers, wall clock, copies inside
     torch.cuda.synchronize()
@@ -222,6 +223,14 @@ def run_ours(args, rank, world):
     res["e2e"] = {"value": e2e_states / t_e2e / 1e9, "unit": "Gstates/s", "h2d_bytes_per_step": int(h2d),
                   "d2h_bytes_per_step": int(d2h)}
     res["fp64"] = fp64
+    # measured rates of the box (context for the roofline)
+    res["probes"] = {
+        "gather_1KiB_GBs": F.ftlm_peak_probe(F.PEAK_GATHER, 2 << 30, 1024) / 1e9,
+        "stream_copy_GBs": F.ftlm_peak_probe(F.PEAK_STREAM, 2 << 30) / 1e9,
+        "ffma32_Tflops": 2 * F.ftlm_peak_probe(F.PEAK_FFMA32) / 1e12,
+        "dfma64_Tflops": 2 * F.ftlm_peak_probe(F.PEAK_DFMA64) / 1e12,
+        "lop3_Tops": F.ftlm_peak_probe(F.PEAK_LOP3) / 1e12,
+    }
     return res
 
 
@@ -234,57 +243,55 @@ def _flip_count(labels, bonds):
     return total
 
 
-def _traffic_record(kernel, dtype_name):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+def _kernel_sha():
     import hashlib
 
     h = hashlib.sha256()
-    for name in ("hv_kernel.cuh", "contract.cuh"):
+    for name in ("hvp.cuh", "ptx.cuh", "contract.cuh"):
         with open(os.path.join(ROOT, "paper_2607_17429_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
-    sha = h.hexdigest()[:16]
+    return h.hexdigest()[:16]
+
+
+def _traffic_record(dtype_name):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    sha = _kernel_sha()
     path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
     try:
         for ln in open(path):
             p = ln.split()
-            if len(p) >= 4 and p[0] == kernel and p[1] == dtype_name and p[3] == sha:
+            if len(p) >= 4 and p[0] == "hvp_kernel" and p[1] == dtype_name and p[3] == sha:
                 return float(p[2])
     except OSError:
         pass
     return None
 
 
-def hv_roofline(prof, dtype_name, flips, G, sum_d2, B, rows, n_reps, K, esize):
-    """Roofline of the dominant kernel (multi-block H·v), per launch.
+def hv_roofline(prof, dtype_name, flips, n_reps, W, B, esize):
+    """Roofline of the dominant kernel (packed H·v), per launch, HBM bound.
 
-    alu: algorithmic lane-operations = flips*|G|*2 (image and min per candidate of the
-         representative search) + flips*sum_k d_k^2*B (contraction FMAs), against the
-         issue peak 152 SMs x 128 lanes x 2.07 GHz.
-    hbm: compulsory bytes = x read once + y written once (sum_k dim_k*B*esize each) +
-         representative tables (n_reps*(8 + 2 + 4K)), against the measured copy bandwidth.
-    The larger fraction is the binding one.
+    Algorithmic bytes = flips * (W*B*e + 20)   [every flipped state's segment, its record and bucket]
+                      + n_reps * (2*W*B*e + 16) [the representative's own rows in, its outputs out, its record]
+    against the measured STREAM copy bandwidth (MEASURED_PEAKS.json hbm_gbs).
     """
     pk, which = peaks()
     if prof["hv_launches"] == 0:
         return None
     t = prof["hv_ms"] / prof["hv_launches"] / 1e3
-    ops = flips * G * 2 + flips * sum_d2 * B
-    alu_peak = 152 * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6
-    byt = 2 * rows * esize + n_reps * (8 + 2 + 4 * K)
-    hbm_peak = float(pk["hbm_gbs"]) * 1e9
-    alu = {"bound": "alu", "achieved": ops / t / 1e12, "peak": alu_peak / 1e12, "unit": "Tops/s",
-           "frac": ops / t / alu_peak, "traffic": _traffic_record("hv_kernel", dtype_name),
-           "algorithmic_per_launch": ops, "peak_source": "derived: 152 SMs x 128 lanes x max SM clock"}
-    hbm = {"bound": "hbm", "achieved": byt / t / 1e9, "peak": hbm_peak / 1e9, "unit": "GB/s",
-           "frac": byt / t / hbm_peak, "traffic": alu["traffic"], "algorithmic_per_launch": byt,
-           "peak_source": f"{which} MEASURED_PEAKS.json hbm_gbs" if which == "measured" else "fallback 6.8 TB/s"}
-    main, alt = (alu, hbm) if alu["frac"] >= hbm["frac"] else (hbm, alu)
-    main["avg_launch_ms"] = t * 1e3
-    return main, alt
+    seg = W * B * esize
+    byt = flips * (seg + 20) + n_reps * (2 * seg + 16)
+    peak = float(pk["hbm_gbs"]) * 1e9
+    return {"bound": "hbm", "achieved": byt / t / 1e9, "peak": peak / 1e9, "unit": "GB/s", "frac": byt / t / peak,
+            "traffic": _traffic_record(dtype_name), "algorithmic_per_launch": byt, "avg_launch_ms": t * 1e3,
+            "peak_source": f"{which} MEASURED_PEAKS.json hbm_gbs" if which == "measured" else "fallback 6.8 TB/s",
+            "kernel_sha": _kernel_sha()}
 
 
-def cpu_baseline(budget_s=12.0):
-    """The oracle's H·v on a bounded sample of representatives of the same workload (H_g block)."""
+def _oracle_worker(args):
+    """One process of the CPU baseline: label-keyed oracle rows for random representatives (spawned)."""
+    seed, budget_s = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    sys.path.insert(0, ROOT)
     from oracle import native
     from oracle.basis import hv_rows_by_label
     from oracle.group import Group
@@ -294,30 +301,45 @@ def cpu_baseline(budget_s=12.0):
     og = Group(c.gens, c.bonds)
     inv = og.element(c.gens[2])
     ir = [i for i, r in enumerate(og.irreps) if r.dim == 5 and r.chars[inv] > 0][0]  # H_g
-    rng = np.random.default_rng(0)
-    reps = []
+    rng = np.random.default_rng(seed)
+    rows = reps = 0
     t0 = time.perf_counter()
-    rows = 0
     while time.perf_counter() - t0 < budget_s:
         batch = []
-        for _ in range(16):
+        for _ in range(8):
             bits = rng.permutation(np.r_[np.ones(15, dtype=np.int64), np.zeros(15, dtype=np.int64)])
             lab = int(sum(int(v) << k for k, v in enumerate(bits)))
             batch.append(native.min_rep(30, 2, og.perms, lab)[0])
         out = hv_rows_by_label(og, ir, c.bonds, 1.0, TWO_S, batch,
                                lambda lab, n: label_keyed_values([lab], n, R, 1)[0])
         rows += sum(0 if y is None else y.shape[0] for y in out)
-        reps += batch
-    dt = time.perf_counter() - t0
-    return {"value": rows * R / dt / 1e9, "unit": "Gstates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(reps)} representatives of the H_g block (random sector states -> orbit minima), "
-                      f"B={R}, {dt:.1f} s, label-keyed oracle rows (Eqs. 15-16)"}
+        reps += len(batch)
+    return rows, reps, time.perf_counter() - t0
+
+
+def cpu_baseline(budget_s=10.0):
+    """The oracle's H·v (FP64, label-keyed rows of the H_g block, B = 8) on every host core, bounded sample."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(1000 + i, budget_s) for i in range(cores)])
+    wall = time.perf_counter() - t0
+    rows = sum(r[0] for r in res)
+    reps = sum(r[1] for r in res)
+    busy = max(r[2] for r in res)
+    return {"value": rows * R / busy / 1e9, "unit": "Gstates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} random representatives of the H_g block (d=5) of the icosidodecahedron M=0 sector, "
+                      f"B={R} right-hand sides, FP64 label-keyed oracle rows (Eqs. 15-16), {cores} spawned "
+                      f"processes x {busy:.1f} s (wall {wall:.1f} s including start-up)"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
@@ -332,17 +354,18 @@ def main():
         K = max(1, args.steps)
         for _ in range(max(0, args.warmup)):
             cpu_baseline(budget_s=2.0)
+        t0 = time.perf_counter()
         vals = [cpu_baseline(budget_s=10.0) for _ in range(K)]
+        ms_step = (time.perf_counter() - t0) * 1e3 / K
         v = float(np.mean([b["value"] for b in vals]))
         cb = dict(vals[-1])
         cb["value"] = v
-        print(json.dumps({"impl": "reference", "metric": "sym-adapted H·v Gstates/s (CPU oracle, FP64)", "value": v,
-                          "unit": "Gstates/s", "n_gpus": args.gpus, "steps": K, "warmup": args.warmup,
-                          "ms_per_step": 10000.0, "higher_is_better": True, "scaling": "weak",
-                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                          "config": {"workload": WORKLOAD}, "cpu_baseline": cb,
-                          "e2e": {"value": v, "unit": "Gstates/s", "h2d_bytes_per_step": 0,
-                                  "d2h_bytes_per_step": 0}}))
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "Gstates/s", "n_gpus": args.gpus,
+                          "steps": K, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": WORKLOAD, "sample": "bounded oracle sample per step"},
+                          "cpu_baseline": cb,
+                          "e2e": {"value": v, "unit": "Gstates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
     if world > 1:
         import torch
@@ -352,27 +375,26 @@ def main():
     if rank != 0:
         return
     prof = res["prof"]
-    rl = hv_roofline(prof, args.dtype, res["flips"], res["G"], res["sum_d2"], R, res["rows"], res["n_reps"],
-                     res["K"], 4 if args.dtype == "f32" else 8)
+    esize = 4 if args.dtype == "f32" else 8
+    rl = hv_roofline(prof, args.dtype, res["flips"], res["n_reps"], res["W"], R, esize)
     line = {
-        "metric": "sym-adapted H·v Gstates/s (mixed FP32 vectors, FP64 alpha/beta)" if args.dtype == "f32"
-        else "sym-adapted H·v Gstates/s (FP64)",
-        "value": res["value"], "unit": "Gstates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": res["ms_all"] / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "metric": METRIC, "value": res["value"], "unit": "Gstates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_all"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": WORKLOAD, "cluster": CLUSTER, "two_s": TWO_S, "two_M": TWO_M, "R": R,
-                   "lanczos_steps": N_STEPS, "blocks": 10, "l2": "inputs larger than L2 (three [dim][8] "
-                   "vectors up to 207 MB each in FP32)", "parallelism": f"replicas{world}"},
-        "blocks_per_hour": 10 * args.steps / (res["ms_all"] / 1e3) * 3600.0 * world,
+                   "lanczos_steps": N_STEPS, "blocks": len(res["dims"]), "precision": "FP32 vectors, FP64 alpha/beta"
+                   if args.dtype == "f32" else "FP64", "l2": "inputs larger than L2 (three packed [41.4M][8] "
+                   "vectors of 1.3 GB each in FP32)", "parallelism": f"replicas{world}"},
+        "blocks_per_hour": len(res["dims"]) * args.steps / (res["ms_all"] / 1e3) * 3600.0 * world,
         "gpu_launches": int(prof["kernel_launches"]),
         "hv_launches": int(prof["hv_launches"]),
         "hv_ms_per_launch": prof["hv_ms"] / max(1, prof["hv_launches"]),
-        "roofline": rl[0] if rl else None,
-        "roofline_other": rl[1] if rl else None,
+        "roofline": rl,
         "E0": res["out"][4],
         "e2e": res["e2e"],
         "clocks": res["clocks"],
         "fp64": res["fp64"],
+        "probes": res["probes"],
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

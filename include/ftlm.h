@@ -73,7 +73,7 @@ typedef struct ftlm_multiblock ftlm_multiblock; /* device: several blocks of one
  *   bonds          [n_bonds][2] host, site pairs of Eq. 1 (i != j)
  *   J              exchange constant of Eq. 1
  *   out            receives the new handle
- * Errors: FTLM_EINVAL, FTLM_ENOTGROUP (not permutations, or |G| > 4096),
+ * Errors: FTLM_EINVAL, FTLM_ENOTGROUP (not permutations, or |G| > 512),
  *         FTLM_EBONDS (Section 3's bond-invariance check), FTLM_EIRREP.
  * Irreps of complex or quaternionic type are listed (fs = 0 or -1) without
  * matrices; blocks of such irreps return FTLM_EUNSUPPORTED.
@@ -174,13 +174,21 @@ void ftlm_basis_free(ftlm_basis *b);
  * a = U(g_e) r' are found by the in-kernel representative search, and r' is
  * looked up in the sorted representative table.
  *   x, y  device [dim][B] of double (FTLM_F64) or float (FTLM_F32), not aliased.
+ * The call lifts x into the block's one-block packed layout, runs the packed
+ * kernel (see ftlm_hv_packed) and lowers the result into y, with scratch from
+ * the stream-ordered allocator (cudaMallocAsync) on cuda_stream.
  * Errors: FTLM_EINVAL (null pointers, B out of range), FTLM_ECUDA (launch).
  * A representative missing from the table (impossible for a consistent basis)
- * sets a device flag reported as FTLM_EINTERNAL by ftlm_basis_check.
+ * sets a device flag reported as FTLM_EINTERNAL by ftlm_basis_check; a
+ * bounded wait that gave up is reported there as FTLM_ETIMEOUT.
  */
 ftlm_status ftlm_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y, void *cuda_stream);
 
-/* Synchronise cuda_stream and report (then clear) the basis's device error flag. */
+/*
+ * Synchronise cuda_stream and report (then clear) the device error word of the
+ * basis's sector: FTLM_ETIMEOUT if a bounded wait gave up, FTLM_EINTERNAL if a
+ * bounds check tripped, FTLM_OK otherwise.
+ */
 ftlm_status ftlm_basis_check(const ftlm_basis *b, void *cuda_stream);
 
 /*
@@ -206,6 +214,80 @@ void ftlm_multiblock_free(ftlm_multiblock *mb);
 ftlm_status ftlm_hv_multi(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, const void *const *x, void *const *y,
                           void *cuda_stream);
 
+/*
+ * Packed layout of a multi-block set: the rows of every block of the set are
+ * interleaved by representative, in lifted coordinates.  Representative i
+ * (ascending label order) owns the W = sum_k d_k rows i W + Z_k + gamma
+ * (Z_k = d_0 + ... + d_{k-1}, gamma < d_k) holding x~_k(r) = V_k(r) x_k(r):
+ * the n_k(r) coefficients of r in block k (Eq. 13's rows of r) mapped into the
+ * d_k-dimensional irrep space by the orthonormal columns of V_r (Eq. 11).  The
+ * map is an isometry, so inner products and norms equal those of the block
+ * vectors; for a trivial stabilizer V_r = I.  Vectors are [rows][B] with rows =
+ * n_reps * W.  One flipped state's representative r' then owns one fixed-size
+ * segment holding every block's coefficients, so one lookup and one gather
+ * serve all blocks of Eq. 15.  Available for the compiled block shapes: a
+ * single block of dimension 1..5, and the full real irrep sets of I_h, O_h and
+ * T_d in canonical irrep order (every set built by ftlm_build_multiblock over
+ * those irreps); rows below 2^32.
+ *   ftlm_multiblock_packed_rows: *rows = n_reps * W (FTLM_EUNSUPPORTED if the
+ *     set has no packed layout).
+ *   ftlm_multiblock_pack: lift per-block vectors (host array of n_blocks device
+ *     pointers, [dim_k][B] each) into one packed device vector [rows][B];
+ *   ftlm_multiblock_unpack: the inverse, x_k(r) = V_k(r)^T x~_k(r).  Both
+ *     synchronise cuda_stream.
+ */
+ftlm_status ftlm_multiblock_packed_rows(const ftlm_multiblock *mb, uint64_t *rows);
+ftlm_status ftlm_multiblock_pack(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, const void *const *blocks,
+                                 void *packed, void *cuda_stream);
+ftlm_status ftlm_multiblock_unpack(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, const void *packed,
+                                   void *const *blocks, void *cuda_stream);
+
+/*
+ * y = H x for every block of the set at once on packed vectors (Eqs. 15-16, the
+ * same arithmetic as ftlm_hv per block, in lifted coordinates):
+ *   y~_k(r) = P_k(r) z_k(r) / sqrt|Stab r| + diag(r) x~_k(r),
+ *   z_k(r)  = sum_{bond, sign} c_a sqrt|Stab r'| rho_k(g_e) x~_k(r'),
+ * with P_k(r) = V_k(r) V_k(r)^T.  One warp per representative searches and
+ * looks up every flipped state once, gathers r''s whole segment (bulk copies
+ * into shared memory when B * element size is a multiple of 16 bytes and x is
+ * 16-byte aligned, lane loads otherwise) and contracts it with every block's
+ * rho(g*)^T.  x, y: device [rows][B], not aliased, 1 <= B <= 32.  Asynchronous
+ * on cuda_stream.  Errors: FTLM_EINVAL, FTLM_EUNSUPPORTED (no packed layout),
+ * FTLM_ECUDA.  Device-side failures (a representative missing from the table,
+ * a bounded wait that gave up) are reported by ftlm_basis_check on any block of
+ * the set.
+ */
+ftlm_status ftlm_hv_packed(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, const void *x, void *y,
+                           void *cuda_stream);
+
+/*
+ * Cycle budget of every bounded device-side wait of the H·v kernels (the
+ * mbarrier waits for bulk copies); 0 restores the default of 2^32 cycles
+ * (about two seconds).  A wait that runs out records FTLM_ETIMEOUT, which
+ * ftlm_basis_check (and the Lanczos calls) return; the warp then waits, with
+ * the default budget, for its copies already in flight before it stops.
+ * Library-wide; meant for tests of the timeout path.
+ */
+ftlm_status ftlm_set_wait_limit(uint64_t cycles);
+
+/*
+ * Test and benchmark inputs at any block size (no counterpart in the paper).
+ * ftlm_fill_label_keyed writes the label-keyed block vector x [dim][B] (device,
+ * dtype, 1 <= B <= 64): the entry of row k of representative r and right-hand
+ * side b is, with L the base-(2s+1) label of r (Eq. 2) and SplitMix64 as
+ * published by Steele, Lea and Flood (OOPSLA'14), all arithmetic mod 2^64,
+ *   z = L * 4096 + k * 64 + b + seed * 0x632BE59BD9B4E019,
+ *   x = (splitmix64(z) >> 11) * 2^-52 - 1  (in [-1, 1), rounded to the dtype).
+ * Any row can be regenerated from its label alone.  Asynchronous on cuda_stream.
+ * ftlm_basis_rows looks up n packed labels (host array): first_row[i] = the
+ * block row of representative labels[i] (-1 if it is not a representative) and
+ * n_rows[i] = its n_Gamma (host outputs).  Synchronises cuda_stream.
+ */
+ftlm_status ftlm_fill_label_keyed(const ftlm_basis *b, ftlm_dtype dtype, int B, uint64_t seed, void *x,
+                                  void *cuda_stream);
+ftlm_status ftlm_basis_rows(const ftlm_basis *b, int n, const uint64_t *labels, int64_t *first_row, int *n_rows,
+                            void *cuda_stream);
+
 /* ---------------------------------------------------------------- Lanczos / FTLM */
 
 /*
@@ -215,23 +297,32 @@ ftlm_status ftlm_hv_multi(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, co
  * counter (row low, row high, chain, 0); Gaussian by Box-Muller on two 53-bit
  * uniforms, or Rademacher +-1 from bit 0; each chain normalised in FP64.
  * Recurrence: w = H v_j; alpha_j = <v_j, w>; w -= alpha_j v_j + beta_j v_{j-1};
- * beta_{j+1} = |w|; v_{j+1} = w / beta_{j+1}; dot products and norms
- * accumulated in FP64 from the stored values (FP32 vectors in FTLM_F32).
+ * beta_{j+1} = |w|; v_{j+1} = w / beta_{j+1}, run on the block's packed
+ * (lifted) vectors with the normalisation folded into scale factors: the
+ * stored vector is u_j = v_j / s_j and alpha_j = s_j^2 <u_j, H u_j>.  Dot
+ * products and norms use exact products of the stored values (FP32 vectors in
+ * FTLM_F32), double-float sums per representative and lane, FP64 beyond; the
+ * order is fixed, so repeated runs give identical coefficients.  The N_L-step
+ * loop is captured in a CUDA graph (FTLM_NO_GRAPH=1 launches it directly).
  * A chain stops after step j when beta_{j+1} <= tol (|alpha_j| + beta_j)
  * (tol = 1e-12 for FP64, 1e-6 for FP32) or when j + 1 = min(n_steps, dim).
  *   alpha, beta   host [R][n_steps]; beta[r][j] = beta_{j+1} (beta[r][m-1] is
  *                 the final residual norm); entries past steps_done are 0.
  *   steps_done    host [R].
- * Device work memory (3 [dim][B] vectors and reduction scratch) is allocated
- * and freed by the call.  Synchronises cuda_stream before returning.
+ * Device work memory (3 packed [rows][B] vectors and reduction scratch) is
+ * allocated and freed by the call.  Synchronises cuda_stream before returning.
+ * FTLM_ETIMEOUT / FTLM_EINTERNAL report device-side failures of the H·v.
  */
 ftlm_status ftlm_lanczos(const ftlm_basis *b, ftlm_dtype dtype, int R, int n_steps, uint64_t seed,
                          uint64_t block_id, ftlm_rng rng, void *cuda_stream, double *alpha, double *beta,
                          int *steps_done);
 
 /*
- * ftlm_lanczos on every block of a multi-block set in lockstep: each step is
- * one ftlm_hv_multi launch plus the per-block recurrence kernels.  Block k
+ * ftlm_lanczos on every block of a multi-block set in lockstep.  Sets with a
+ * packed layout run the packed path of ftlm_lanczos_sets (one H·v launch and
+ * one update launch per step for all blocks, captured in a CUDA graph);
+ * others take one ftlm_hv_multi launch plus per-block recurrence kernels per
+ * step.  Block k
  * draws its start vectors with block_ids[k]; results equal ftlm_lanczos per
  * block up to rounding.  alpha, beta: host [n_blocks][R][n_steps];
  * steps_done: host [n_blocks][R].
@@ -239,6 +330,20 @@ ftlm_status ftlm_lanczos(const ftlm_basis *b, ftlm_dtype dtype, int R, int n_ste
 ftlm_status ftlm_lanczos_multi(const ftlm_multiblock *mb, ftlm_dtype dtype, int R, int n_steps, uint64_t seed,
                                const uint64_t *block_ids, ftlm_rng rng, void *cuda_stream, double *alpha,
                                double *beta, int *steps_done);
+
+/*
+ * ftlm_lanczos_multi on several packed sets at once, for instance every S^z
+ * sector of a cluster (Section 2.2's block-factorised FTLM): all sets must
+ * come from the same group (same permutations, bonds, J and irreps), the same
+ * spin and the same irreps in the same order, and have a packed layout.  Each
+ * kernel of a step is one launch over the representatives of every set (the
+ * sets are the parts of a persistent tile walk), and the step loop is one
+ * CUDA graph.  block_ids: host [n_sets][K]; alpha, beta: host
+ * [n_sets][K][R][n_steps]; steps_done: host [n_sets][K][R].
+ */
+ftlm_status ftlm_lanczos_sets(int n_sets, const ftlm_multiblock *const *sets, ftlm_dtype dtype, int R, int n_steps,
+                              uint64_t seed, const uint64_t *block_ids, ftlm_rng rng, void *cuda_stream,
+                              double *alpha, double *beta, int *steps_done);
 
 /*
  * Ritz values and weights of tridiagonal matrices on the GPU in FP64 (implicit

@@ -218,6 +218,7 @@ void free_sector(ftlm_sector *s) {
     cudaFree(s->d_stab_id);
     cudaFree(s->d_bucket);
     cudaFree(s->d_lut);
+    cudaFree(s->d_lut2);
     cudaFree(s->d_pos);
     cudaFree(s->d_dtab);
     cudaFree(s->d_bonds);
@@ -249,6 +250,19 @@ ftlm_status build_search_tables(ftlm_sector *s) {
             for (int g = 0; g < kMaxG; ++g)
                 dt[(size_t)e * kMaxG + g] = (1u << pi(g, s->grp.bonds[2 * e])) | (1u << pi(g, s->grp.bonds[2 * e + 1]));
         FTLM_CUDA(cudaMalloc((void **)&s->d_lut, lut.size() * 4));
+        s->n_chunks2 = (N + 1) / 2;  // 2-site chunks for the packed kernel
+        std::vector<uint32_t> lut2((size_t)s->n_chunks2 * 4 * kMaxG, 0);
+        for (int c = 0; c < s->n_chunks2; ++c)
+            for (int v = 0; v < 4; ++v)
+                for (int g = 0; g < kMaxG; ++g) {
+                    uint32_t img = 0;
+                    for (int t = 0; t < 2; ++t)
+                        if (((v >> t) & 1) && 2 * c + t < N) img |= 1u << pi(g, 2 * c + t);
+                    lut2[((size_t)c * 4 + v) * kMaxG + g] = img;
+                }
+        FTLM_CUDA(cudaMalloc((void **)&s->d_lut2, lut2.size() * 4));
+        FTLM_CUDA(cudaMemcpy(s->d_lut2, lut2.data(), lut2.size() * 4, cudaMemcpyHostToDevice));
+        s->device_bytes += lut2.size() * 4;
         FTLM_CUDA(cudaMemcpy(s->d_lut, lut.data(), lut.size() * 4, cudaMemcpyHostToDevice));
         FTLM_CUDA(cudaMalloc(&s->d_dtab, dt.size() * 4));
         FTLM_CUDA(cudaMemcpy(s->d_dtab, dt.data(), dt.size() * 4, cudaMemcpyHostToDevice));
@@ -465,6 +479,7 @@ void free_block(ftlm_basis *b) {
     cudaFree(b->d_Vf);
     cudaFree(b->d_rhoT);
     cudaFree(b->d_rhoTf);
+    packed_set_free(b->ps);
     if (b->sec) sector_release(b->sec);
     delete b;
 }
@@ -522,7 +537,8 @@ ftlm_status build_block_impl(ftlm_sector *s, int irrep, cudaStream_t stream, ftl
     ftlm_status st = exclusive_scan(NGammaOf{s->d_stab_id, b->d_ntab}, s->n_reps, b->d_off, stream, &dim);
     if (st != FTLM_OK) return st;
     b->dim = dim;
-    return FTLM_OK;
+    const ftlm_basis *one[1] = {b};
+    return packed_set_build(s, 1, one, stream, &b->ps);
 }
 
 __global__ void interleave_offsets(const uint64_t *const *offs, int K, uint64_t n_reps, uint64_t *offm) {
@@ -538,6 +554,7 @@ void free_multiblock(ftlm_multiblock *mb) {
     cudaFree(mb->d_ntab);
     cudaFree(mb->d_rhoT);
     cudaFree(mb->d_rhoTf);
+    packed_set_free(mb->ps);
     if (mb->sec) sector_release(mb->sec);
     delete mb;
 }
@@ -593,6 +610,11 @@ ftlm_status build_multiblock_impl(ftlm_sector *s, int n, const int *irreps, cuda
     interleave_offsets<<<(unsigned)((s->n_reps + 255) / 256), 256, 0, stream>>>(d_offs.p, n, s->n_reps, mb->d_offm);
     FTLM_CUDA(cudaGetLastError());
     FTLM_CUDA(cudaStreamSynchronize(stream));
+    if (n <= kPMaxK && packed_shape_id(n, mb->d.data()) >= 0) {
+        ftlm_status st = packed_set_build(s, n, mb->blocks.data(), stream, &mb->ps);
+        if (st != FTLM_OK) return st;
+        mb->device_bytes += mb->ps->device_bytes;
+    }
     return FTLM_OK;
 }
 
@@ -744,6 +766,7 @@ ftlm_status ftlm_basis_check(const ftlm_basis *b, void *cuda_stream) {
     FTLM_CUDA(cudaMemcpy(&err, b->sec->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err) {
         FTLM_CUDA(cudaMemset(b->sec->d_err, 0, sizeof(int)));
+        if (err & 8) return fail(FTLM_ETIMEOUT, "a bounded device wait gave up (code %d)", err);
         return fail(FTLM_EINTERNAL, "device bounds check tripped (code %d)", err);
     }
     return FTLM_OK;

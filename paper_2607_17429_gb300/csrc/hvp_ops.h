@@ -1,0 +1,52 @@
+// Compiled packed H·v kernels: one entry per (shape, elements per lane, label width).
+#pragma once
+
+#include <vector>
+
+#include "hvp.cuh"
+
+namespace ftlm {
+
+// Shape ids: one block of dimension 1..5, and the full real irrep sets of I_h,
+// O_h and T_d in canonical irrep order (dimensions ascending).
+enum { kShapeD1 = 0, kShapeD2, kShapeD3, kShapeD4, kShapeD5, kShapeIh, kShapeOh, kShapeTd, kNumShapes };
+using ShapeIh = Shape<1, 1, 3, 3, 3, 3, 4, 4, 5, 5>;
+using ShapeOh = Shape<1, 1, 1, 1, 2, 2, 3, 3, 3, 3>;
+using ShapeTd = Shape<1, 1, 2, 3, 3>;
+
+template <typename VT>
+struct HvpOps {
+    int (*occupancy)(const HvpArgs<VT> &, int warps, int nbuf);
+    ftlm_status (*launch)(HvpArgs<VT>, const HvpGeom &, cudaStream_t);
+    int max_threads;
+};
+
+#define FTLM_HVP_OPS(VT, SH, GPL, HALF) \
+    HvpOps<VT> { &hvp_occupancy_t<VT, SH, GPL, HALF>, &hvp_launch_t<VT, SH, GPL, HALF>, hvp_max_threads<VT, SH>() }
+
+template <typename VT>
+struct HvpPlan {
+    HvpArgs<VT> a;
+    HvpGeom geo;
+    const HvpOps<VT> *ops = nullptr;
+    uint64_t rows_total = 0;          // packed rows over all parts (profiling)
+    std::vector<uint64_t> tile0, ntile;  // per part: first tile and tile count
+};
+
+// packed.cu
+template <typename VT>
+void hvp_part_of(const ftlm_sector *s, const PackedSet *ps, const ftlm_basis *const *blocks, const VT *x, VT *y,
+                 HvpPart<VT> &p);
+template <typename VT>
+ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpPart<VT>> &parts, int B,
+                     HvpPlan<VT> &plan);
+template <typename VT>
+ftlm_status hvp_launch_plan(const HvpPlan<VT> &plan, double *dot_part, cudaStream_t stream, bool timed);
+
+// null if the combination is not compiled (gpl: 2 for |G| <= 64, 4 for |G| <= 128)
+const HvpOps<float> *hvp_ops_single_f32(int shape, int gpl, bool half);
+const HvpOps<float> *hvp_ops_multi_f32(int shape, int gpl, bool half);
+const HvpOps<double> *hvp_ops_single_f64(int shape, int gpl, bool half);
+const HvpOps<double> *hvp_ops_multi_f64(int shape, int gpl, bool half);
+
+}  // namespace ftlm

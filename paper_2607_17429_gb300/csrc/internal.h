@@ -17,6 +17,39 @@ constexpr int kMaxGHost = 512;  // group order supported by the host group modul
 constexpr int kMaxD = 5;        // irrep dimension supported on the GPU path
 constexpr int kMaxBonds = 64;   // bonds per cluster on the GPU path
 constexpr int kMaxB = 32;       // right-hand sides per H·v launch
+constexpr int kPMaxK = 10;      // blocks per packed set (compile-time shapes)
+
+// Record of one representative in a packed set: label, first row of its
+// segment in the packed vector, stabilizer subgroup id.
+struct alignas(16) HvRec {
+    uint64_t label;
+    uint32_t off;
+    uint32_t sid;
+};
+
+// Packed set: K blocks of one sector whose rows are interleaved by
+// representative, in lifted coordinates: representative r owns the W = sum_k
+// d_k rows (k, gamma), gamma < d_k, holding V_k(r) x_k(r) (Eq. 11's V_r maps a
+// block's n_k(r) coefficients of r isometrically into the irrep space).  K = 1
+// is a single block.  Built by packed.cu.
+struct PackedSet {
+    int K = 0;
+    int W = 0;          // sum of d_k: rows of a representative with trivial stabilizer
+    int shape = -1;     // compiled shape id (see packed.cu), -1 if none matches
+    int dims[kPMaxK] = {};
+    uint64_t rows = 0;  // packed rows = n_reps * W
+    HvRec *d_rec = nullptr;         // [n_reps]: label, off = index * W, stabilizer id
+    uint8_t *d_ntab = nullptr;      // [n_sid][K] n_k(sid)
+    uint8_t *d_wtab = nullptr;      // [n_sid] sum_k n_k(sid)
+    double *d_P[kPMaxK] = {};       // block k: [n_sid][d_k][d_k] projector V V^T
+    float *d_Pf[kPMaxK] = {};
+    double *d_rhoT = nullptr;       // concatenated padded rho(g)^T tables
+    float *d_rhoTf = nullptr;
+    int rho_total = 0, rho_totalf = 0;
+    int rho_off[kPMaxK] = {}, rho_offf[kPMaxK] = {};
+    std::vector<uint8_t> h_wtab;
+    size_t device_bytes = 0;
+};
 
 ftlm_status fail(ftlm_status st, const char *fmt, ...);
 void clear_error();
@@ -71,6 +104,8 @@ struct ftlm_sector {
     // H·v search tables
     uint32_t *d_lut = nullptr;   // s = 1/2: [nchunk][16][kMaxG] image of a 4-site nibble under g
     int n_chunks = 0;
+    uint32_t *d_lut2 = nullptr;  // s = 1/2: [nchunk2][4][kMaxG] image of a 2-site chunk under g
+    int n_chunks2 = 0;
     uint8_t *d_pos = nullptr;    // general s: [kMaxG][64] bit position of site k's field after g
     void *d_dtab = nullptr;      // [n_bonds][kMaxG] u32 XOR masks (s = 1/2) or int64 deltas (general)
     uint8_t *d_bonds = nullptr;  // [n_bonds][2] site pairs
@@ -94,6 +129,7 @@ struct ftlm_basis {
     float *d_rhoTf = nullptr;
     int rho_elems = 0, rho_elemsf = 0;  // padded table sizes (FP64, FP32)
     std::vector<uint8_t> h_ntab;
+    ftlm::PackedSet *ps = nullptr;  // the block as a one-block packed set
     size_t device_bytes = 0;
 };
 
@@ -108,9 +144,14 @@ struct ftlm_multiblock {
     float *d_rhoTf = nullptr;
     int rho_total = 0, rho_totalf = 0;
     std::vector<int> d, rho_off, rho_offf;
+    ftlm::PackedSet *ps = nullptr;  // packed layout of the whole set (null if its shape is not compiled)
     size_t device_bytes = 0;
 };
 
 namespace ftlm {
 void sector_release(ftlm_sector *s);
+// packed.cu
+ftlm_status packed_set_build(ftlm_sector *s, int K, const ftlm_basis *const *blocks, void *stream, PackedSet **out);
+void packed_set_free(PackedSet *ps);
+int packed_shape_id(int K, const int *dims);
 }

@@ -11,12 +11,20 @@
 #include <vector>
 
 #include "common.cuh"
+#include "philox.cuh"
 #include "ritz_thermo.cuh"
 
 namespace ftlm {
 
-ftlm_status hv_launch_f64(const ftlm_basis *bs, int B, const double *x, double *y, cudaStream_t stream);
-ftlm_status hv_launch_f32(const ftlm_basis *bs, int B, const float *x, float *y, cudaStream_t stream);
+struct LzSetIn {
+    const ftlm_sector *sec;
+    const PackedSet *ps;
+    const ftlm_basis *const *blocks;
+    const uint64_t *block_ids;
+};
+template <typename VT>
+ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps, uint64_t seed, int rng,
+                           cudaStream_t stream, double *alpha, double *beta, int *steps_done);
 ftlm_status hv_multi_launch_f64(const ftlm_multiblock *mb, int B, const double *const *x, double *const *y,
                                cudaStream_t stream);
 ftlm_status hv_multi_launch_f32(const ftlm_multiblock *mb, int B, const float *const *x, float *const *y,
@@ -26,34 +34,6 @@ namespace {
 
 constexpr int kRedBlocks = kNumSMs * 4;  // fixed reduction grid (deterministic order)
 constexpr int kRedThreads = 256;
-
-// ---------------------------------------------------------------- Philox4x32-10 (Salmon et al., SC'11)
-
-struct U4 {
-    uint32_t x, y, z, w;
-};
-
-__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
-    }
-    return c;
-}
-
-__device__ __forceinline__ double start_value(uint64_t row, uint32_t chain, uint32_t k0, uint32_t k1, int rng) {
-    const U4 o = philox4x32_10(U4{(uint32_t)row, (uint32_t)(row >> 32), chain, 0u}, k0, k1);
-    if (rng == FTLM_RADEMACHER) return (o.x & 1u) ? -1.0 : 1.0;
-    const double u1 = ((double)(((uint64_t)(o.x >> 5) << 26) | (o.y >> 6)) + 0.5) * 0x1p-53;
-    const double u2 = (double)(((uint64_t)(o.z >> 5) << 26) | (o.w >> 6)) * 0x1p-53;
-    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
-}
 
 // Threads of a reduction block are (row lane r, column b): t = r * B + b.
 __device__ __forceinline__ int red_rows(int B) { return kRedThreads / B; }
@@ -174,101 +154,6 @@ __global__ void fin_beta(const double *p, int B, int j, int m_max, double tol, L
         st.beta_prev[b] = bn;
         st.scale[b] = 1.0 / bn;
     }
-}
-
-template <typename VT>
-ftlm_status hv_any(const ftlm_basis *b, int B, const VT *x, VT *y, cudaStream_t st);
-template <>
-ftlm_status hv_any<double>(const ftlm_basis *b, int B, const double *x, double *y, cudaStream_t st) {
-    return hv_launch_f64(b, B, x, y, st);
-}
-template <>
-ftlm_status hv_any<float>(const ftlm_basis *b, int B, const float *x, float *y, cudaStream_t st) {
-    return hv_launch_f32(b, B, x, y, st);
-}
-
-template <typename VT>
-ftlm_status lanczos_impl(const ftlm_basis *bs, int R, int n_steps, uint64_t seed, uint64_t block_id, int rng,
-                         cudaStream_t stream, double *alpha, double *beta, int *steps_done) {
-    const uint64_t dim = bs->dim;
-    const int Bmax = std::min(R, kMaxB);
-    const int m_max = (int)std::min<uint64_t>((uint64_t)n_steps, dim);
-    const double tol = sizeof(VT) == 8 ? 1e-12 : 1e-6;
-    for (int r = 0; r < R; ++r) {
-        steps_done[r] = 0;
-        for (int j = 0; j < n_steps; ++j) alpha[(size_t)r * n_steps + j] = beta[(size_t)r * n_steps + j] = 0.0;
-    }
-    if (dim == 0 || m_max == 0) return FTLM_OK;
-    DevBuf<VT> v0, v1, v2;
-    FTLM_CUDA(v0.alloc(dim * Bmax));
-    FTLM_CUDA(v1.alloc(dim * Bmax));
-    FTLM_CUDA(v2.alloc(dim * Bmax));
-    DevBuf<double> partials, dstate;
-    DevBuf<int> istate;
-    FTLM_CUDA(partials.alloc((size_t)kRedBlocks * Bmax));
-    FTLM_CUDA(dstate.alloc((size_t)2 * m_max * Bmax + 2 * Bmax));
-    FTLM_CUDA(istate.alloc((size_t)2 * Bmax));
-    LzState st;
-    st.alpha = dstate.p;
-    st.beta = dstate.p + (size_t)m_max * Bmax;
-    st.beta_prev = dstate.p + (size_t)2 * m_max * Bmax;
-    st.scale = st.beta_prev + Bmax;
-    st.active = istate.p;
-    st.steps = istate.p + Bmax;
-    std::vector<double> ha((size_t)m_max * Bmax), hb((size_t)m_max * Bmax);
-    std::vector<int> hs(Bmax);
-    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)block_id;
-    const int scale_blocks = kNumSMs * 8;
-    for (int chain0 = 0; chain0 < R; chain0 += Bmax) {
-        const int Bc = std::min(Bmax, R - chain0);
-        const int B = Bc;  // vectors are [dim][Bc]
-        VT *vp = v0.p, *v = v1.p, *w = v2.p;
-        FTLM_CUDA(cudaMemsetAsync(dstate.p, 0, ((size_t)2 * m_max * Bmax + 2 * Bmax) * sizeof(double), stream));
-        FTLM_CUDA(cudaMemsetAsync(vp, 0, dim * B * sizeof(VT), stream));
-        count_launch();
-        lz_random<VT><<<kRedBlocks, kRedThreads, 0, stream>>>(v, dim, B, Bc, (uint32_t)chain0, k0, k1, rng,
-                                                              partials.p);
-        count_launch();
-        fin_norm<<<1, 32, 0, stream>>>(partials.p, B, st);
-        count_launch();
-        lz_scale<VT><<<scale_blocks, 256, 0, stream>>>(v, dim, B, st);
-        FTLM_CUDA(cudaGetLastError());
-        for (int j = 0; j < m_max; ++j) {
-            ftlm_status s = hv_any<VT>(bs, B, v, w, stream);
-            if (s != FTLM_OK) return s;
-            count_launch();
-            lz_dot<VT><<<kRedBlocks, kRedThreads, 0, stream>>>(v, w, dim, B, partials.p);
-            count_launch();
-            fin_alpha<<<1, 32, 0, stream>>>(partials.p, B, j, st);
-            count_launch();
-            lz_update<VT><<<kRedBlocks, kRedThreads, 0, stream>>>(w, v, vp, dim, B, j, st, partials.p);
-            count_launch();
-            fin_beta<<<1, 32, 0, stream>>>(partials.p, B, j, m_max, tol, st);
-            count_launch();
-            lz_scale<VT><<<scale_blocks, 256, 0, stream>>>(w, dim, B, st);
-            FTLM_CUDA(cudaGetLastError());
-            VT *t = vp;
-            vp = v;
-            v = w;
-            w = t;
-        }
-        FTLM_CUDA(cudaMemcpyAsync(ha.data(), st.alpha, (size_t)m_max * B * 8, cudaMemcpyDeviceToHost, stream));
-        FTLM_CUDA(cudaMemcpyAsync(hb.data(), st.beta, (size_t)m_max * B * 8, cudaMemcpyDeviceToHost, stream));
-        FTLM_CUDA(cudaMemcpyAsync(hs.data(), st.steps, (size_t)B * 4, cudaMemcpyDeviceToHost, stream));
-        FTLM_CUDA(cudaStreamSynchronize(stream));
-        int err = 0;
-        FTLM_CUDA(cudaMemcpy(&err, bs->sec->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (err) return fail(FTLM_EINTERNAL, "device bounds check tripped in H·v (code %d)", err);
-        for (int b = 0; b < Bc; ++b) {
-            const int r = chain0 + b;
-            steps_done[r] = hs[b];
-            for (int j = 0; j < hs[b]; ++j) {
-                alpha[(size_t)r * n_steps + j] = ha[(size_t)j * B + b];
-                beta[(size_t)r * n_steps + j] = hb[(size_t)j * B + b];
-            }
-        }
-    }
-    return FTLM_OK;
 }
 
 template <typename VT>
@@ -394,24 +279,16 @@ using namespace ftlm;
 
 extern "C" {
 
-ftlm_status ftlm_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y, void *cuda_stream) {
-    if (!b || !x || !y) return fail(FTLM_EINVAL, "NULL argument");
-    if (B < 1 || B > kMaxB) return fail(FTLM_EINVAL, "B must be in 1..%d", kMaxB);
-    if (b->dim == 0) return FTLM_OK;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    if (dtype == FTLM_F64) return hv_launch_f64(b, B, (const double *)x, (double *)y, st);
-    if (dtype == FTLM_F32) return hv_launch_f32(b, B, (const float *)x, (float *)y, st);
-    return fail(FTLM_EINVAL, "unknown dtype");
-}
-
 ftlm_status ftlm_lanczos(const ftlm_basis *b, ftlm_dtype dtype, int R, int n_steps, uint64_t seed, uint64_t block_id,
                          ftlm_rng rng, void *cuda_stream, double *alpha, double *beta, int *steps_done) {
     if (!b || !alpha || !beta || !steps_done) return fail(FTLM_EINVAL, "NULL argument");
     if (R < 1 || n_steps < 1 || n_steps > kMaxSteps) return fail(FTLM_EINVAL, "R >= 1 and 1 <= n_steps <= 512");
     if (rng != FTLM_GAUSS && rng != FTLM_RADEMACHER) return fail(FTLM_EINVAL, "unknown rng");
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    if (dtype == FTLM_F64) return lanczos_impl<double>(b, R, n_steps, seed, block_id, rng, st, alpha, beta, steps_done);
-    if (dtype == FTLM_F32) return lanczos_impl<float>(b, R, n_steps, seed, block_id, rng, st, alpha, beta, steps_done);
+    const ftlm_basis *one[1] = {b};
+    std::vector<LzSetIn> sets{{b->sec, b->ps, one, &block_id}};
+    if (dtype == FTLM_F64) return lanczos_packed<double>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done);
+    if (dtype == FTLM_F32) return lanczos_packed<float>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done);
     return fail(FTLM_EINVAL, "unknown dtype");
 }
 
@@ -435,10 +312,46 @@ ftlm_status ftlm_lanczos_multi(const ftlm_multiblock *mb, ftlm_dtype dtype, int 
     if (R < 1 || n_steps < 1 || n_steps > kMaxSteps) return fail(FTLM_EINVAL, "R >= 1 and 1 <= n_steps <= 512");
     if (rng != FTLM_GAUSS && rng != FTLM_RADEMACHER) return fail(FTLM_EINVAL, "unknown rng");
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (mb->ps) {  // packed layout: one launch per kernel for all blocks
+        std::vector<LzSetIn> sets{{mb->sec, mb->ps, mb->blocks.data(), block_ids}};
+        if (dtype == FTLM_F64)
+            return lanczos_packed<double>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done);
+        if (dtype == FTLM_F32) return lanczos_packed<float>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done);
+        return fail(FTLM_EINVAL, "unknown dtype");
+    }
     if (dtype == FTLM_F64)
         return lanczos_multi_impl<double>(mb, R, n_steps, seed, block_ids, rng, st, alpha, beta, steps_done);
     if (dtype == FTLM_F32)
         return lanczos_multi_impl<float>(mb, R, n_steps, seed, block_ids, rng, st, alpha, beta, steps_done);
+    return fail(FTLM_EINVAL, "unknown dtype");
+}
+
+ftlm_status ftlm_lanczos_sets(int n_sets, const ftlm_multiblock *const *sets, ftlm_dtype dtype, int R, int n_steps,
+                              uint64_t seed, const uint64_t *block_ids, ftlm_rng rng, void *cuda_stream,
+                              double *alpha, double *beta, int *steps_done) {
+    if (n_sets < 1 || !sets || !block_ids || !alpha || !beta || !steps_done) return fail(FTLM_EINVAL, "bad arguments");
+    if (R < 1 || n_steps < 1 || n_steps > kMaxSteps) return fail(FTLM_EINVAL, "R >= 1 and 1 <= n_steps <= 512");
+    if (rng != FTLM_GAUSS && rng != FTLM_RADEMACHER) return fail(FTLM_EINVAL, "unknown rng");
+    const ftlm_multiblock *m0 = sets[0];
+    if (!m0 || !m0->ps) return fail(FTLM_EUNSUPPORTED, "set 0 has no packed layout");
+    const int K = m0->K;
+    std::vector<LzSetIn> in;
+    for (int i = 0; i < n_sets; ++i) {
+        const ftlm_multiblock *m = sets[i];
+        if (!m || !m->ps) return fail(FTLM_EUNSUPPORTED, "set %d has no packed layout", i);
+        const GroupData &g0 = m0->sec->grp, &g = m->sec->grp;
+        bool same = m->K == K && m->ps->shape == m0->ps->shape && m->sec->two_s == m0->sec->two_s &&
+                    g.perms == g0.perms && g.bonds == g0.bonds && g.J == g0.J && g.irreps.size() == g0.irreps.size();
+        for (int k = 0; same && k < K; ++k) {
+            same = m->blocks[k]->irrep == m0->blocks[k]->irrep &&
+                   g.irreps[m->blocks[k]->irrep].rho == g0.irreps[m0->blocks[k]->irrep].rho;
+        }
+        if (!same) return fail(FTLM_EINVAL, "set %d differs from set 0 in group, spin, bonds or irreps", i);
+        in.push_back({m->sec, m->ps, m->blocks.data(), block_ids + (size_t)i * K});
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (dtype == FTLM_F64) return lanczos_packed<double>(in, R, n_steps, seed, rng, st, alpha, beta, steps_done);
+    if (dtype == FTLM_F32) return lanczos_packed<float>(in, R, n_steps, seed, rng, st, alpha, beta, steps_done);
     return fail(FTLM_EINVAL, "unknown dtype");
 }
 

@@ -1,0 +1,542 @@
+// FTLM Lanczos chains on packed sets (Section 2.2 of arXiv 2607.17429), batched
+// through one packed H·v launch per step, with the step loop captured in a
+// CUDA graph.
+//
+// The vectors are kept unnormalised: u_j with v_j = s_j u_j.  One step j is
+//   A  y = H u_j (packed H·v) with <u_j, y> per (block, chain) fused into
+//      the H·v epilogue;
+//   fA alpha_j = s_j^2 <u_j, y>; coefficients (s_j, alpha_j s_j, beta_j s_{j-1});
+//   U  w = s_j y - alpha_j s_j u_j - beta_j s_{j-1} u_{j-1}  (= H v_j - alpha_j v_j
+//      - beta_j v_{j-1}), written over y, with |w|^2 per (block, chain);
+//   fB beta_{j+1} = |w|, stop test, s_{j+1} = 1 / beta_{j+1}, u_{j+1} = w.
+// Dot products and norms: exact products, double-float sums per representative
+// and lane (FP32 vectors) or FP64 (FP64 vectors), FP64 across lanes and CTAs in a
+// fixed order, so repeated runs give identical coefficients.  A chain stops
+// after step j when beta_{j+1} <= tol (|alpha_j| + beta_j) (tol 1e-12 for FP64,
+// 1e-6 for FP32 vectors) or when j + 1 = min(n_steps, dim).
+//
+// Several packed sets of the same group and shape (for instance every S^z
+// sector of a cluster) run as the parts of one launch per kernel.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "hvp_ops.h"
+#include "philox.cuh"
+#include "ritz_thermo.cuh"
+
+namespace ftlm {
+
+void hv_profile_add(double ms, uint64_t rows);
+unsigned long long wait_limit_cycles();
+
+namespace {
+
+constexpr int kLzThreads = 256;
+
+template <typename VT>
+struct LzPart {
+    uint64_t n_reps;
+    uint64_t tile0;
+    const HvRec *rec;
+    const uint8_t *ntab;           // [n_sid][K] n_k(sid)
+    const VT *V[kPMaxK];           // block k: [n_sid][d_k][d_k] (Eq. 11), lifts the start vectors
+    const uint64_t *boff[kPMaxK];  // block k's row offsets [n_reps] (start-vector counters)
+    uint32_t key1[kPMaxK];         // Philox key word 1 of block k (block id)
+    int entry0;                    // index of (part, block 0, chain 0) in the state arrays: p * K * B
+    VT *y;                         // update: y in, w out; start vectors: output
+    const VT *u, *up;
+};
+
+template <typename VT>
+struct LzArgs {
+    int n_parts;
+    LzPart<VT> part0;
+    const LzPart<VT> *parts;
+    uint64_t n_tiles;
+    int tile_reps;
+    int B, BT, lgBT;
+    int dims[kPMaxK], zoff[kPMaxK];
+    int has_prev, rng;
+    uint32_t chain0, key0;
+    const VT *coef;        // [entries][3]: s_j, alpha_j s_j, beta_j s_{j-1}
+    double *norm_part;     // [n_parts][gridDim.x][K][B]
+};
+
+// MODE 0: start vectors u_0 (Philox per block row index and chain, lifted by
+// V_k(r)); MODE 1: the update.  Both accumulate |.|^2 per (block, chain) and
+// write per-CTA partials.  Rows of representative r: r W + Z_k + gamma.
+template <typename VT, int K, int MODE>
+__global__ void __launch_bounds__(kLzThreads) lzp_kernel(const __grid_constant__ LzArgs<VT> a) {
+    __shared__ double red[kPMaxK * 32];
+    const int warps = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int B = a.B, BT = a.BT;
+    const int Q = 32 >> a.lgBT;
+    const int b = lane & (BT - 1), fg = lane >> a.lgBT;
+    for (int i = threadIdx.x; i < K * B; i += blockDim.x) red[i] = 0.0;
+    __syncthreads();
+    DotAcc<VT> acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k].zero();
+    VT cy[K], cu[K], cp[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) cy[k] = cu[k] = cp[k] = (VT)0;
+    int cur = -1;
+    auto flush = [&](int p) {
+        double v[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            v[k] = acc[k].value();
+            for (int w = BT; w < 32; w <<= 1) v[k] += __shfl_xor_sync(kFullMask, v[k], w);
+        }
+        for (int w = 0; w < warps; ++w) {
+            __syncthreads();
+            if (wid == w && lane < B) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) red[k * B + lane] += v[k];
+            }
+        }
+        __syncthreads();
+        double *dst = a.norm_part + ((size_t)p * gridDim.x + blockIdx.x) * K * B;
+        for (int i = threadIdx.x; i < K * B; i += blockDim.x) {
+            dst[i] = red[i];
+            red[i] = 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k].zero();
+    };
+    for (uint64_t t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        int p = 0;
+        if (a.n_parts > 1) {
+            int lo = 0, hi = a.n_parts - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.parts[mid].tile0 <= t)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            p = lo;
+        }
+        const LzPart<VT> &P = a.n_parts == 1 ? a.part0 : a.parts[p];
+        if (p != cur) {
+            if (cur >= 0) flush(cur);
+            cur = p;
+            if (MODE == 1 && b < B) {
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const VT *c = a.coef + ((size_t)P.entry0 + k * B + b) * 3;
+                    cy[k] = c[0];
+                    cu[k] = c[1];
+                    cp[k] = c[2];
+                }
+            }
+        }
+        const uint64_t r0 = (t - P.tile0) * (uint64_t)a.tile_reps;
+        const uint64_t r1 = min(r0 + (uint64_t)a.tile_reps, P.n_reps);
+        for (uint64_t rep = r0 + wid; rep < r1; rep += warps) {
+            const HvRec rr = P.rec[rep];
+            const int sid = (int)rr.sid;
+            if (b >= B) continue;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int D = a.dims[k];
+                for (int gam = fg; gam < D; gam += Q) {
+                    const size_t e = ((size_t)rr.off + a.zoff[k] + gam) * B + b;
+                    if (MODE == 0) {
+                        const uint64_t row0 = __ldg(P.boff[k] + rep);
+                        VT v;
+                        if (sid == 0) {
+                            v = (VT)start_value(row0 + (uint64_t)gam, a.chain0 + (uint32_t)b, a.key0, P.key1[k], a.rng);
+                        } else {  // lift the n_k(r) coefficients: V_k(r) x_k(r)
+                            const int nk = __ldg(P.ntab + sid * K + k);
+                            const VT *Vr = P.V[k] + ((size_t)sid * D + gam) * D;
+                            v = (VT)0;
+                            for (int q = 0; q < nk; ++q)
+                                v += __ldg(Vr + q) *
+                                     (VT)start_value(row0 + (uint64_t)q, a.chain0 + (uint32_t)b, a.key0, P.key1[k], a.rng);
+                        }
+                        P.y[e] = v;
+                        acc[k].add(v, v);
+                    } else {
+                        VT w = cy[k] * P.y[e] - cu[k] * __ldg(P.u + e);
+                        if (a.has_prev) w -= cp[k] * __ldg(P.up + e);
+                        P.y[e] = w;
+                        acc[k].add(w, w);
+                    }
+                }
+            }
+        }
+    }
+    if (cur >= 0) flush(cur);
+}
+
+struct LzState {
+    double *alpha, *beta;       // [n_steps][entries]
+    double *s, *s_prev, *bprev; // [entries]
+    int *active, *steps;        // [entries]
+    const int *m_max;           // [n_parts * K]
+    double *coef64;             // [entries][3]
+    float *coef32;              // [entries][3]
+};
+
+// One CTA per part, one thread per (block, chain).  Sums the per-CTA partials of
+// the CTAs that processed tiles of the part (tile order fixed, so the sum is too).
+// mode 0: start-vector norms; 1: alpha_j and the update coefficients; 2: beta_{j+1}.
+__global__ void lzp_finalize(int mode, int j, int K, int B, int grid, const uint64_t *tile0, const uint64_t *ntile,
+                             const double *part, LzState st, double tol) {
+    const int p = blockIdx.x, t = threadIdx.x;
+    if (t >= K * B) return;
+    const int k = t / B, b = t % B;
+    const size_t e = ((size_t)p * K + k) * B + b;
+    const uint64_t nt = ntile[p], t0 = tile0[p];
+    double sum = 0.0;
+    if (nt >= (uint64_t)grid) {
+        for (int c = 0; c < grid; ++c) sum += part[(((size_t)p * grid + c) * K + k) * B + b];
+    } else {
+        for (uint64_t i = 0; i < nt; ++i) {
+            const int c = (int)((t0 + i) % (uint64_t)grid);
+            sum += part[(((size_t)p * grid + c) * K + k) * B + b];
+        }
+    }
+    const size_t E = (size_t)gridDim.x * K * B;
+    if (mode == 0) {
+        const double n = sqrt(sum);
+        const bool on = n > 0.0 && st.m_max[p * K + k] > 0;
+        st.s[e] = on ? 1.0 / n : 0.0;
+        st.s_prev[e] = 0.0;
+        st.bprev[e] = 0.0;
+        st.active[e] = on ? 1 : 0;
+        st.steps[e] = 0;
+    } else if (mode == 1) {
+        double c0 = 0.0, c1 = 0.0, c2 = 0.0, al = 0.0;
+        if (st.active[e]) {
+            const double s = st.s[e];
+            al = s * s * sum;
+            c0 = s;
+            c1 = al * s;
+            c2 = j > 0 ? st.bprev[e] * st.s_prev[e] : 0.0;
+        }
+        st.alpha[(size_t)j * E + e] = al;
+        st.coef64[3 * e] = c0;
+        st.coef64[3 * e + 1] = c1;
+        st.coef64[3 * e + 2] = c2;
+        st.coef32[3 * e] = (float)c0;
+        st.coef32[3 * e + 1] = (float)c1;
+        st.coef32[3 * e + 2] = (float)c2;
+    } else {
+        if (!st.active[e]) {
+            st.beta[(size_t)j * E + e] = 0.0;
+            return;
+        }
+        const double bn = sqrt(sum);
+        const double al = st.alpha[(size_t)j * E + e];
+        st.beta[(size_t)j * E + e] = bn;
+        if (j + 1 >= st.m_max[p * K + k] || bn <= tol * (fabs(al) + st.bprev[e])) {
+            st.active[e] = 0;
+            st.steps[e] = j + 1;
+        } else {
+            st.s_prev[e] = st.s[e];
+            st.s[e] = 1.0 / bn;
+            st.bprev[e] = bn;
+        }
+    }
+}
+
+template <typename VT, int MODE>
+ftlm_status lzp_launch(int K, const LzArgs<VT> &a, int grid, cudaStream_t st) {
+    count_launch();
+    switch (K) {
+        case 1: lzp_kernel<VT, 1, MODE><<<grid, kLzThreads, 0, st>>>(a); break;
+        case 5: lzp_kernel<VT, 5, MODE><<<grid, kLzThreads, 0, st>>>(a); break;
+        case 10: lzp_kernel<VT, 10, MODE><<<grid, kLzThreads, 0, st>>>(a); break;
+        default: return fail(FTLM_EUNSUPPORTED, "no recurrence kernel for %d blocks", K);
+    }
+    FTLM_CUDA(cudaGetLastError());
+    return FTLM_OK;
+}
+
+}  // namespace
+
+// One packed set taking part in a Lanczos launch: sector, packed set, its K
+// blocks and their block ids (Philox key word 1).
+struct LzSetIn {
+    const ftlm_sector *sec;
+    const PackedSet *ps;
+    const ftlm_basis *const *blocks;
+    const uint64_t *block_ids;
+};
+
+// R chains on every block of every set, n_steps steps.  alpha, beta: host
+// [n_sets][K][R][n_steps]; steps_done: host [n_sets][K][R].
+template <typename VT>
+ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps, uint64_t seed, int rng,
+                           cudaStream_t stream, double *alpha, double *beta, int *steps_done) {
+    const int P = (int)sets.size();
+    const PackedSet *ps0 = sets[0].ps;
+    const int K = ps0->K;
+    const size_t out_n = (size_t)P * K * R;
+    for (size_t i = 0; i < out_n; ++i) steps_done[i] = 0;
+    for (size_t i = 0; i < out_n * n_steps; ++i) alpha[i] = beta[i] = 0.0;
+    const int Bmax = std::min(R, kMaxB);
+    std::vector<uint64_t> row0(P + 1, 0);
+    std::vector<int> m_max((size_t)P * K);
+    int m_all = 0;
+    for (int p = 0; p < P; ++p) {
+        row0[p + 1] = row0[p] + sets[p].ps->rows;
+        for (int k = 0; k < K; ++k) {
+            m_max[(size_t)p * K + k] = (int)std::min<uint64_t>((uint64_t)n_steps, sets[p].blocks[k]->dim);
+            m_all = std::max(m_all, m_max[(size_t)p * K + k]);
+        }
+    }
+    if (m_all == 0) return FTLM_OK;
+    const uint64_t rows = row0[P];
+    DevBuf<VT> vb[3];
+    for (int q = 0; q < 3; ++q) FTLM_CUDA(vb[q].alloc(std::max<uint64_t>(rows, 1) * Bmax));
+    const size_t E = (size_t)P * K * Bmax;
+    DevBuf<double> dstate;
+    DevBuf<float> fstate;
+    DevBuf<int> istate;
+    FTLM_CUDA(dstate.alloc(2 * (size_t)n_steps * E + 6 * E));
+    FTLM_CUDA(fstate.alloc(3 * E));
+    FTLM_CUDA(istate.alloc(2 * E + (size_t)P * K));
+    LzState st;
+    st.alpha = dstate.p;
+    st.beta = dstate.p + (size_t)n_steps * E;
+    st.s = st.beta + (size_t)n_steps * E;
+    st.s_prev = st.s + E;
+    st.bprev = st.s_prev + E;
+    st.coef64 = st.bprev + E;
+    st.coef32 = fstate.p;
+    st.active = istate.p;
+    st.steps = istate.p + E;
+    st.m_max = istate.p + 2 * E;
+    FTLM_CUDA(cudaMemcpyAsync(istate.p + 2 * E, m_max.data(), m_max.size() * sizeof(int), cudaMemcpyHostToDevice,
+                              stream));
+    int dev = 0, sms = kNumSMs;
+    FTLM_CUDA(cudaGetDevice(&dev));
+    FTLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const double tol = sizeof(VT) == 8 ? 1e-12 : 1e-6;
+    const char *ng = getenv("FTLM_NO_GRAPH");
+    const bool use_graph = !(ng && strcmp(ng, "1") == 0);
+    std::vector<double> ha, hb;
+    std::vector<int> hs;
+
+    for (int chain0 = 0; chain0 < R; chain0 += Bmax) {
+        const int B = std::min(Bmax, R - chain0);
+        const size_t EB = (size_t)P * K * B;  // entries of this batch
+        // ---- H·v plans for the three rotations: x = vb[j % 3], y = vb[(j + 1) % 3]
+        HvpPlan<VT> plan[3];
+        std::vector<HvpPart<VT>> hparts[3];
+        DevBuf<HvpPart<VT>> d_hparts[3];
+        for (int q = 0; q < 3; ++q) {
+            hparts[q].resize(P);
+            for (int p = 0; p < P; ++p)
+                hvp_part_of<VT>(sets[p].sec, sets[p].ps, sets[p].blocks, vb[q].p + row0[p] * B,
+                                vb[(q + 1) % 3].p + row0[p] * B, hparts[q][p]);
+            ftlm_status s0 = hvp_plan<VT>(sets[0].sec, ps0, hparts[q], B, plan[q]);
+            if (s0 != FTLM_OK) return s0;
+            plan[q].rows_total = rows;
+            if (P > 1) {
+                FTLM_CUDA(d_hparts[q].alloc(P));
+                FTLM_CUDA(cudaMemcpyAsync(d_hparts[q].p, hparts[q].data(), P * sizeof(HvpPart<VT>),
+                                          cudaMemcpyHostToDevice, stream));
+                plan[q].a.parts = d_hparts[q].p;
+            }
+        }
+        const int hv_grid = plan[0].geo.grid;
+        DevBuf<double> hv_part, lz_part;
+        FTLM_CUDA(hv_part.alloc((size_t)P * hv_grid * K * B));
+        DevBuf<uint64_t> tiles;  // hv tile0, hv ntile, lz tile0, lz ntile
+        FTLM_CUDA(tiles.alloc(4 * (size_t)P));
+        // ---- recurrence kernels: tiles of 64 representatives, up to 8 CTAs per SM
+        const int lz_tile = 64;
+        std::vector<uint64_t> tinfo(4 * (size_t)P);
+        uint64_t lz_tiles = 0;
+        for (int p = 0; p < P; ++p) {
+            tinfo[p] = plan[0].tile0[p];
+            tinfo[P + p] = plan[0].ntile[p];
+            const uint64_t nt = (sets[p].sec->n_reps + lz_tile - 1) / lz_tile;
+            tinfo[2 * P + p] = lz_tiles;
+            tinfo[3 * P + p] = nt;
+            lz_tiles += nt;
+        }
+        const int lz_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(lz_tiles, (uint64_t)sms * 8));
+        FTLM_CUDA(lz_part.alloc((size_t)P * lz_grid * K * B));
+        FTLM_CUDA(cudaMemcpyAsync(tiles.p, tinfo.data(), tinfo.size() * 8, cudaMemcpyHostToDevice, stream));
+        std::vector<LzPart<VT>> lparts[4];  // rotations 0..2 (update) and 3 (start vectors)
+        DevBuf<LzPart<VT>> d_lparts[4];
+        LzArgs<VT> la[4];
+        for (int q = 0; q < 4; ++q) {
+            lparts[q].resize(P);
+            for (int p = 0; p < P; ++p) {
+                LzPart<VT> &lp = lparts[q][p];
+                memset(&lp, 0, sizeof(lp));
+                lp.n_reps = sets[p].sec->n_reps;
+                lp.tile0 = tinfo[2 * P + p];
+                lp.rec = sets[p].ps->d_rec;
+                lp.ntab = sets[p].ps->d_ntab;
+                for (int k = 0; k < K; ++k) {
+                    lp.V[k] = sizeof(VT) == 8 ? reinterpret_cast<const VT *>(sets[p].blocks[k]->d_V)
+                                              : reinterpret_cast<const VT *>(sets[p].blocks[k]->d_Vf);
+                    lp.boff[k] = sets[p].blocks[k]->d_off;
+                    lp.key1[k] = (uint32_t)sets[p].block_ids[k];
+                }
+                lp.entry0 = p * K * B;
+                if (q < 3) {  // step j with j % 3 == q: y = vb[(q+1)%3], u = vb[q], up = vb[(q+2)%3]
+                    lp.y = vb[(q + 1) % 3].p + row0[p] * B;
+                    lp.u = vb[q].p + row0[p] * B;
+                    lp.up = vb[(q + 2) % 3].p + row0[p] * B;
+                } else {
+                    lp.y = vb[0].p + row0[p] * B;
+                }
+            }
+            LzArgs<VT> &A = la[q];
+            memset(&A, 0, sizeof(A));
+            A.n_parts = P;
+            if (P == 1) {
+                A.part0 = lparts[q][0];
+            } else {
+                FTLM_CUDA(d_lparts[q].alloc(P));
+                FTLM_CUDA(cudaMemcpyAsync(d_lparts[q].p, lparts[q].data(), P * sizeof(LzPart<VT>),
+                                          cudaMemcpyHostToDevice, stream));
+                A.parts = d_lparts[q].p;
+            }
+            A.n_tiles = lz_tiles;
+            A.tile_reps = lz_tile;
+            A.B = B;
+            A.BT = plan[0].a.BT;
+            A.lgBT = plan[0].a.lgBT;
+            int z = 0;
+            for (int k = 0; k < K; ++k) {
+                A.dims[k] = ps0->dims[k];
+                A.zoff[k] = z;
+                z += ps0->dims[k];
+            }
+            A.rng = rng;
+            A.chain0 = (uint32_t)chain0;
+            A.key0 = (uint32_t)seed;
+            A.coef = sizeof(VT) == 8 ? reinterpret_cast<const VT *>(st.coef64) : reinterpret_cast<const VT *>(st.coef32);
+            A.norm_part = lz_part.p;
+            A.has_prev = 0;
+        }
+        const uint64_t *hv_t0 = tiles.p, *hv_nt = tiles.p + P, *lz_t0 = tiles.p + 2 * P, *lz_nt = tiles.p + 3 * P;
+        // ---- start vectors and their norms
+        ftlm_status s1 = lzp_launch<VT, 0>(K, la[3], lz_grid, stream);
+        if (s1 != FTLM_OK) return s1;
+        count_launch();
+        lzp_finalize<<<P, K * B, 0, stream>>>(0, 0, K, B, lz_grid, lz_t0, lz_nt, lz_part.p, st, tol);
+        FTLM_CUDA(cudaGetLastError());
+        // ---- the step loop (captured once on a private stream, replayed once on the caller's)
+        const bool prof = profiling_on();
+        std::vector<cudaEvent_t> ev;
+        auto steps = [&](cudaStream_t ss, bool capture) -> ftlm_status {
+            for (int j = 0; j < m_all; ++j) {
+                const int q = j % 3;
+                if (prof) {
+                    cudaEvent_t e0, e1;
+                    FTLM_CUDA(cudaEventCreate(&e0));
+                    FTLM_CUDA(cudaEventCreate(&e1));
+                    ev.push_back(e0);
+                    ev.push_back(e1);
+                    FTLM_CUDA(capture ? cudaEventRecordWithFlags(e0, ss, cudaEventRecordExternal)
+                                      : cudaEventRecord(e0, ss));
+                }
+                ftlm_status s2 = hvp_launch_plan<VT>(plan[q], hv_part.p, ss, false);
+                if (s2 != FTLM_OK) return s2;
+                if (prof)
+                    FTLM_CUDA(capture ? cudaEventRecordWithFlags(ev.back(), ss, cudaEventRecordExternal)
+                                      : cudaEventRecord(ev.back(), ss));
+                count_launch();
+                lzp_finalize<<<P, K * B, 0, ss>>>(1, j, K, B, hv_grid, hv_t0, hv_nt, hv_part.p, st, tol);
+                FTLM_CUDA(cudaGetLastError());
+                LzArgs<VT> A = la[q];
+                A.has_prev = j > 0;
+                s2 = lzp_launch<VT, 1>(K, A, lz_grid, ss);
+                if (s2 != FTLM_OK) return s2;
+                count_launch();
+                lzp_finalize<<<P, K * B, 0, ss>>>(2, j, K, B, lz_grid, lz_t0, lz_nt, lz_part.p, st, tol);
+                FTLM_CUDA(cudaGetLastError());
+            }
+            return FTLM_OK;
+        };
+        if (use_graph) {
+            cudaStream_t cap = nullptr;
+            FTLM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (ce != cudaSuccess) {
+                cudaStreamDestroy(cap);
+                return fail(FTLM_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+            }
+            ftlm_status s3 = steps(cap, true);
+            ce = cudaStreamEndCapture(cap, &graph);  // always end the capture, even after a failed launch
+            cudaStreamDestroy(cap);
+            if (s3 != FTLM_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return s3;
+            }
+            if (ce != cudaSuccess) return fail(FTLM_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return fail(FTLM_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+            ce = cudaGraphLaunch(exec, stream);
+            cudaError_t ce2 = cudaStreamSynchronize(stream);
+            cudaGraphExecDestroy(exec);
+            if (ce != cudaSuccess || ce2 != cudaSuccess)
+                return fail(FTLM_ECUDA, "graph launch: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+        } else {
+            ftlm_status s3 = steps(stream, false);
+            if (s3 != FTLM_OK) return s3;
+            FTLM_CUDA(cudaStreamSynchronize(stream));
+        }
+        if (prof) {
+            for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) hv_profile_add(ms, rows * B);
+            }
+            for (auto e : ev) cudaEventDestroy(e);
+        }
+        // ---- results of the batch
+        ha.resize((size_t)n_steps * E);
+        hb.resize((size_t)n_steps * E);
+        hs.resize(E);
+        FTLM_CUDA(cudaMemcpyAsync(ha.data(), st.alpha, (size_t)n_steps * E * 8, cudaMemcpyDeviceToHost, stream));
+        FTLM_CUDA(cudaMemcpyAsync(hb.data(), st.beta, (size_t)n_steps * E * 8, cudaMemcpyDeviceToHost, stream));
+        FTLM_CUDA(cudaMemcpyAsync(hs.data(), st.steps, E * sizeof(int), cudaMemcpyDeviceToHost, stream));
+        FTLM_CUDA(cudaStreamSynchronize(stream));
+        for (int p = 0; p < P; ++p) {
+            int err = 0;
+            FTLM_CUDA(cudaMemcpy(&err, sets[p].sec->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+            if (err) {
+                cudaMemset(sets[p].sec->d_err, 0, sizeof(int));
+                if (err & kErrWaitTimeout) return fail(FTLM_ETIMEOUT, "a bounded device wait gave up in H·v");
+                return fail(FTLM_EINTERNAL, "device bounds check tripped in H·v (code %d)", err);
+            }
+        }
+        for (int p = 0; p < P; ++p)
+            for (int k = 0; k < K; ++k)
+                for (int b = 0; b < B; ++b) {
+                    const size_t e = ((size_t)p * K + k) * B + b;
+                    const size_t o = ((size_t)p * K + k) * R + chain0 + b;
+                    const int m = hs[e];
+                    steps_done[o] = m;
+                    for (int jj = 0; jj < m; ++jj) {
+                        alpha[o * n_steps + jj] = ha[(size_t)jj * EB + e];
+                        beta[o * n_steps + jj] = hb[(size_t)jj * EB + e];
+                    }
+                }
+    }
+    return FTLM_OK;
+}
+
+template ftlm_status lanczos_packed<float>(const std::vector<LzSetIn> &, int, int, uint64_t, int, cudaStream_t,
+                                           double *, double *, int *);
+template ftlm_status lanczos_packed<double>(const std::vector<LzSetIn> &, int, int, uint64_t, int, cudaStream_t,
+                                            double *, double *, int *);
+
+}  // namespace ftlm

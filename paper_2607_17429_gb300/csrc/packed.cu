@@ -1,0 +1,577 @@
+// Packed sets (K irrep blocks of one sector, rows interleaved by representative
+// in lifted coordinates) and the entry points of the packed H·v: ftlm_hv (one
+// block), ftlm_hv_packed, ftlm_multiblock_pack / _unpack, ftlm_set_wait_limit.
+//
+// Construction (Section 3's two phases): the irrep-independent records of the
+// sector (label, stabilizer id) get the segment offset r * W of every
+// representative; per stabilizer id the set keeps n_k (Section 2.3), their sum,
+// and the projector V_k V_k^T of every block (Eq. 11).  Lifting a block vector,
+// x~_k(r) = V_k(r) x_k(r), and lowering it back, x_k(r) = V_k(r)^T x~_k(r), are
+// the pack and unpack copies.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "hvp_ops.h"
+
+namespace ftlm {
+
+namespace {
+
+struct ShapeDef {
+    int K;
+    int d[kPMaxK];
+};
+const ShapeDef kShapeDefs[kNumShapes] = {
+    {1, {1}}, {1, {2}}, {1, {3}}, {1, {4}}, {1, {5}},
+    {10, {1, 1, 3, 3, 3, 3, 4, 4, 5, 5}},
+    {10, {1, 1, 1, 1, 2, 2, 3, 3, 3, 3}},
+    {5, {1, 1, 2, 3, 3}},
+};
+
+std::atomic<unsigned long long> g_wait_limit{kDrainCycles};
+
+__global__ void fill_records(const uint64_t *labels, const uint16_t *stab_id, uint64_t n, int W, HvRec *rec) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    HvRec r;
+    r.label = labels[i];
+    r.off = (uint32_t)(i * (uint64_t)W);
+    r.sid = stab_id[i];
+    rec[i] = r;
+}
+
+struct LiftArgs {
+    uint64_t n_reps;
+    int K, W, B, to_packed;
+    int dims[kPMaxK], zoff[kPMaxK];
+    const uint8_t *ntab;
+    const HvRec *rec;
+    const uint64_t *boff[kPMaxK];
+    const void *V[kPMaxK];
+    void *blk[kPMaxK];
+};
+
+// packed (lifted) <-> per-block vectors: one thread per (representative, right-hand side)
+template <typename VT>
+__global__ void lift_rows(const __grid_constant__ LiftArgs a, VT *packed) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= a.n_reps * (uint64_t)a.B) return;
+    const uint64_t rep = t / a.B;
+    const int b = (int)(t % a.B), B = a.B;
+    const HvRec r = a.rec[rep];
+    for (int k = 0; k < a.K; ++k) {
+        const int d = a.dims[k];
+        const int n = a.ntab[r.sid * a.K + k];
+        const VT *V = reinterpret_cast<const VT *>(a.V[k]) + (size_t)r.sid * d * d;
+        VT *blk = reinterpret_cast<VT *>(a.blk[k]);
+        const uint64_t o = a.boff[k][rep];
+        VT *pk = packed + ((uint64_t)r.off + a.zoff[k]) * B + b;
+        if (a.to_packed) {
+            for (int gm = 0; gm < d; ++gm) {
+                VT v = (VT)0;
+                if (r.sid == 0)
+                    v = blk[(o + gm) * B + b];
+                else
+                    for (int q = 0; q < n; ++q) v += V[gm * d + q] * blk[(o + q) * B + b];
+                pk[(size_t)gm * B] = v;
+            }
+        } else {
+            for (int q = 0; q < n; ++q) {
+                VT v = (VT)0;
+                if (r.sid == 0)
+                    v = pk[(size_t)q * B];
+                else
+                    for (int gm = 0; gm < d; ++gm) v += V[gm * d + q] * pk[(size_t)gm * B];
+                blk[(o + q) * B + b] = v;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int packed_shape_id(int K, const int *dims) {
+    for (int s = 0; s < kNumShapes; ++s) {
+        if (kShapeDefs[s].K != K) continue;
+        bool eq = true;
+        for (int k = 0; k < K; ++k) eq = eq && kShapeDefs[s].d[k] == dims[k];
+        if (eq) return s;
+    }
+    return -1;
+}
+
+unsigned long long wait_limit_cycles() { return g_wait_limit.load(); }
+
+void packed_set_free(PackedSet *ps) {
+    if (!ps) return;
+    cudaFree(ps->d_rec);
+    cudaFree(ps->d_ntab);
+    cudaFree(ps->d_wtab);
+    for (int k = 0; k < kPMaxK; ++k) {
+        cudaFree(ps->d_P[k]);
+        cudaFree(ps->d_Pf[k]);
+    }
+    cudaFree(ps->d_rhoT);
+    cudaFree(ps->d_rhoTf);
+    delete ps;
+}
+
+ftlm_status packed_set_build(ftlm_sector *s, int K, const ftlm_basis *const *blocks, void *stream_v, PackedSet **out) {
+    cudaStream_t stream = (cudaStream_t)stream_v;
+    *out = nullptr;
+    if (K < 1 || K > kPMaxK) return fail(FTLM_EINVAL, "packed set: 1..%d blocks", kPMaxK);
+    PackedSet *ps = new (std::nothrow) PackedSet();
+    if (!ps) return fail(FTLM_ENOMEM, "host allocation failed");
+    struct Guard {
+        PackedSet *p;
+        ~Guard() { packed_set_free(p); }
+    } guard{ps};
+    ps->K = K;
+    for (int k = 0; k < K; ++k) {
+        ps->dims[k] = blocks[k]->d;
+        ps->W += blocks[k]->d;
+    }
+    ps->shape = packed_shape_id(K, ps->dims);
+    const size_t ns = s->stab_elems.size();
+    std::vector<uint8_t> ntab(ns * K), wtab(ns);
+    for (size_t t = 0; t < ns; ++t) {
+        int o = 0;
+        for (int k = 0; k < K; ++k) {
+            ntab[t * K + k] = blocks[k]->h_ntab[t];
+            o += blocks[k]->h_ntab[t];
+        }
+        wtab[t] = (uint8_t)o;
+    }
+    ps->h_wtab = wtab;
+    // projectors P = V V^T per block and stabilizer id (FP64 from the FP64 V, then rounded)
+    for (int k = 0; k < K; ++k) {
+        const int d = blocks[k]->d;
+        std::vector<double> V(ns * d * d), Pm(ns * d * d);
+        FTLM_CUDA(cudaMemcpy(V.data(), blocks[k]->d_V, V.size() * 8, cudaMemcpyDeviceToHost));
+        for (size_t t = 0; t < ns; ++t)
+            for (int i = 0; i < d; ++i)
+                for (int j = 0; j < d; ++j) {
+                    double acc = 0.0;
+                    for (int q = 0; q < d; ++q) acc += V[(t * d + i) * d + q] * V[(t * d + j) * d + q];
+                    Pm[(t * d + i) * d + j] = acc;
+                }
+        std::vector<float> Pf(Pm.begin(), Pm.end());
+        FTLM_CUDA(cudaMalloc((void **)&ps->d_P[k], Pm.size() * 8));
+        FTLM_CUDA(cudaMalloc((void **)&ps->d_Pf[k], Pf.size() * 4));
+        FTLM_CUDA(cudaMemcpy(ps->d_P[k], Pm.data(), Pm.size() * 8, cudaMemcpyHostToDevice));
+        FTLM_CUDA(cudaMemcpy(ps->d_Pf[k], Pf.data(), Pf.size() * 4, cudaMemcpyHostToDevice));
+        ps->device_bytes += Pm.size() * 12;
+    }
+    // rho(g)^T tables of the blocks, concatenated (FP64 and FP32), padded rows as in contract.cuh
+    std::vector<double> rho;
+    std::vector<float> rhof;
+    const int G = s->G;
+    for (int k = 0; k < K; ++k) {
+        const Irrep &ir = s->grp.irreps[blocks[k]->irrep];
+        const int d = ir.dim, RP = rho_row(d);
+        ps->rho_off[k] = (int)rho.size();
+        ps->rho_offf[k] = (int)rhof.size();
+        rho.resize(rho.size() + rho_table_elems<double>(G, d), 0.0);
+        rhof.resize(rhof.size() + rho_table_elems<float>(G, d), 0.0f);
+        for (int g = 0; g < G; ++g)
+            for (int r = 0; r < d; ++r)
+                for (int c = 0; c < d; ++c) {
+                    const double v = ir.rho[((size_t)g * d + c) * d + r];
+                    rho[ps->rho_off[k] + ((size_t)g * d + r) * RP + c] = v;
+                    rhof[ps->rho_offf[k] + ((size_t)g * d + r) * RP + c] = (float)v;
+                }
+    }
+    ps->rho_total = (int)rho.size();
+    ps->rho_totalf = (int)rhof.size();
+    FTLM_CUDA(cudaMalloc((void **)&ps->d_ntab, ntab.size() + 1));
+    FTLM_CUDA(cudaMalloc((void **)&ps->d_wtab, wtab.size() + 1));
+    FTLM_CUDA(cudaMalloc((void **)&ps->d_rhoT, rho.size() * 8 + 16));
+    FTLM_CUDA(cudaMalloc((void **)&ps->d_rhoTf, rhof.size() * 4 + 16));
+    FTLM_CUDA(cudaMalloc((void **)&ps->d_rec, s->n_reps * sizeof(HvRec) + sizeof(HvRec)));
+    ps->device_bytes += ntab.size() + wtab.size() + rho.size() * 8 + rhof.size() * 4 + s->n_reps * sizeof(HvRec);
+    FTLM_CUDA(cudaMemcpyAsync(ps->d_ntab, ntab.data(), ntab.size(), cudaMemcpyHostToDevice, stream));
+    FTLM_CUDA(cudaMemcpyAsync(ps->d_wtab, wtab.data(), wtab.size(), cudaMemcpyHostToDevice, stream));
+    FTLM_CUDA(cudaMemcpyAsync(ps->d_rhoT, rho.data(), rho.size() * 8, cudaMemcpyHostToDevice, stream));
+    FTLM_CUDA(cudaMemcpyAsync(ps->d_rhoTf, rhof.data(), rhof.size() * 4, cudaMemcpyHostToDevice, stream));
+    const uint64_t rows = s->n_reps * (uint64_t)ps->W;
+    if (rows >= 0xffffffffull)
+        return fail(FTLM_EUNSUPPORTED, "packed set has %llu rows (limit 2^32 - 1)", (unsigned long long)rows);
+    ps->rows = rows;
+    if (s->n_reps) {
+        count_launch();
+        fill_records<<<(unsigned)((s->n_reps + 255) / 256), 256, 0, stream>>>(s->d_labels, s->d_stab_id, s->n_reps,
+                                                                               ps->W, ps->d_rec);
+        FTLM_CUDA(cudaGetLastError());
+    }
+    FTLM_CUDA(cudaStreamSynchronize(stream));
+    guard.p = nullptr;
+    *out = ps;
+    return FTLM_OK;
+}
+
+// ---------------------------------------------------------------- launch assembly
+
+template <typename VT>
+const HvpOps<VT> *hvp_ops(int shape, int gpl, bool half);
+template <>
+const HvpOps<float> *hvp_ops<float>(int shape, int gpl, bool half) {
+    return shape <= kShapeD5 ? hvp_ops_single_f32(shape, gpl, half) : hvp_ops_multi_f32(shape, gpl, half);
+}
+template <>
+const HvpOps<double> *hvp_ops<double>(int shape, int gpl, bool half) {
+    return shape <= kShapeD5 ? hvp_ops_single_f64(shape, gpl, half) : hvp_ops_multi_f64(shape, gpl, half);
+}
+
+// Sector-wide part of the arguments (search tables, coefficients, irreps of the set).
+template <typename VT>
+void hvp_fill_common(const ftlm_sector *s, const PackedSet *ps, int B, HvpArgs<VT> &a) {
+    memset(&a, 0, sizeof(a));
+    a.N = s->N;
+    a.G = s->G;
+    a.n_bonds = s->grp.n_bonds();
+    a.bits = s->bits;
+    a.two_s = s->two_s;
+    a.n_chunks = s->n_chunks2;
+    a.J = (VT)s->grp.J;
+    const double sp = 0.5 * s->two_s, ss1 = sp * (sp + 1.0);
+    for (int i = 0; i < 8; ++i) {
+        const double mm = i - sp;
+        const double u = ss1 - mm * (mm + 1.0), dn = ss1 - mm * (mm - 1.0);
+        a.up[i] = (VT)(u > 0 ? sqrt(u) : 0.0);
+        a.dn[i] = (VT)(dn > 0 ? sqrt(dn) : 0.0);
+    }
+    a.lut2 = s->d_lut2;
+    a.pos = s->d_pos;
+    a.dtab = s->d_dtab;
+    a.bonds = s->d_bonds;
+    if (sizeof(VT) == 4) {
+        a.rhoT = reinterpret_cast<const VT *>(ps->d_rhoTf);
+        a.rho_total = ps->rho_totalf;
+        for (int k = 0; k < ps->K; ++k) a.rho_off[k] = ps->rho_offf[k];
+    } else {
+        a.rhoT = reinterpret_cast<const VT *>(ps->d_rhoT);
+        a.rho_total = ps->rho_total;
+        for (int k = 0; k < ps->K; ++k) a.rho_off[k] = ps->rho_off[k];
+    }
+    int bt = 1, lg = 0;
+    while (bt < B) {
+        bt <<= 1;
+        ++lg;
+    }
+    a.B = B;
+    a.BT = bt;
+    a.lgBT = lg;
+    const int per16 = 16 / (int)sizeof(VT);
+    a.slot_elems = (ps->W * B + per16 - 1) / per16 * per16;
+    const int Q = 32 / bt;
+    int st = Q * a.slot_elems;
+    st = std::max(st, ps->W * bt);
+    a.stage_elems = (st + per16 - 1) / per16 * per16;
+    a.wait_limit = wait_limit_cycles();
+    a.err = s->d_err;
+}
+
+template <typename VT>
+void hvp_part_of(const ftlm_sector *s, const PackedSet *ps, const ftlm_basis *const *blocks, const VT *x, VT *y,
+                 HvpPart<VT> &p) {
+    memset(&p, 0, sizeof(p));
+    p.n_reps = s->n_reps;
+    p.rec = ps->d_rec;
+    p.bucket = s->d_bucket;
+    p.n_buckets = s->n_buckets;
+    p.bucket_shift = s->bucket_shift;
+    p.n_sid = (int)s->stab_elems.size();
+    p.wtab = ps->d_wtab;
+    if (sizeof(VT) == 4) {
+        p.sqrtS = reinterpret_cast<const VT *>(blocks[0]->d_sqrtSf);
+        for (int k = 0; k < ps->K; ++k) p.Pj[k] = reinterpret_cast<const VT *>(ps->d_Pf[k]);
+    } else {
+        p.sqrtS = reinterpret_cast<const VT *>(blocks[0]->d_sqrtS);
+        for (int k = 0; k < ps->K; ++k) p.Pj[k] = reinterpret_cast<const VT *>(ps->d_P[k]);
+    }
+    p.x = x;
+    p.y = y;
+}
+
+// Geometry: the most warps (up to the kernel's bound) whose shared memory fits;
+// at that warp count, rho tables in shared memory before reading them through
+// L1 (FP32), the own-row prefetch before plain loads, and the most staging
+// buffers in flight (bulk-copy path, up to kMaxBuf).  FTLM_HV_WARPS,
+// FTLM_HV_NBUF, FTLM_HV_RHO (smem|l1) and FTLM_HV_OWN (0|1) override the choice.
+template <typename VT>
+ftlm_status hvp_choose_geom(const HvpOps<VT> *ops, HvpArgs<VT> a, bool tma, HvpGeom &geo) {
+    int dev = 0, sms = kNumSMs;
+    FTLM_CUDA(cudaGetDevice(&dev));
+    FTLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const char *ew = getenv("FTLM_HV_WARPS");
+    const char *eb = getenv("FTLM_HV_NBUF");
+    const char *er = getenv("FTLM_HV_RHO");
+    const char *eo = getenv("FTLM_HV_OWN");
+    const int max_warps = ops->max_threads / 32;
+    const int want_warps = ew ? std::min(atoi(ew), max_warps) : 0;
+    const int want_nbuf = eb ? std::max(1, std::min(atoi(eb), kMaxBuf)) : 0;
+    std::vector<int> rho_opts = sizeof(VT) == 4 ? std::vector<int>{1, 0} : std::vector<int>{0};
+    if (er && sizeof(VT) == 4) rho_opts = {strcmp(er, "l1") == 0 ? 0 : 1};
+    std::vector<int> own_opts = tma ? std::vector<int>{1, 0} : std::vector<int>{0};
+    if (eo && tma) own_opts = {atoi(eo) ? 1 : 0};
+    a.tma = tma ? 1 : 0;
+    for (int warps = max_warps; warps >= 2; warps -= 2) {
+        if (want_warps > 0 && warps != want_warps) continue;
+        for (int rho : rho_opts)
+            for (int own : own_opts) {
+                const int nb_hi = tma ? (want_nbuf ? want_nbuf : kMaxBuf) : 1;
+                const int nb_lo = tma && want_nbuf ? want_nbuf : 1;
+                for (int nbuf = nb_hi; nbuf >= nb_lo; --nbuf) {
+                    a.rho_smem = rho;
+                    a.own = own;
+                    const int per_sm = ops->occupancy(a, warps, nbuf);
+                    if (per_sm < 1) continue;
+                    geo.warps = warps;
+                    geo.nbuf = nbuf;
+                    geo.tma = tma ? 1 : 0;
+                    geo.rho_smem = rho;
+                    geo.own = own;
+                    geo.tile_reps = warps * 4;
+                    geo.grid = sms * per_sm;
+                    return FTLM_OK;
+                }
+            }
+    }
+    return fail(FTLM_EUNSUPPORTED, "packed H·v does not fit in shared memory");
+}
+
+// Plan of a packed H·v launch over parts that share the set's shape and group:
+// arguments, geometry and tile order.  One part travels inside the kernel
+// arguments; several need a device array of descriptors (HvpPlan::a.parts),
+// filled by the caller before the launch and kept alive until it ends.
+template <typename VT>
+ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpPart<VT>> &parts, int B,
+                     HvpPlan<VT> &plan) {
+    if (ps->shape < 0) return fail(FTLM_EUNSUPPORTED, "no compiled packed kernel for this block set");
+    HvpArgs<VT> &a = plan.a;
+    hvp_fill_common<VT>(s, ps, B, a);
+    const int gpl = s->G <= 64 ? 2 : 4;
+    plan.ops = hvp_ops<VT>(ps->shape, gpl, s->half);
+    if (!plan.ops)
+        return fail(FTLM_EUNSUPPORTED, "no compiled packed kernel for shape %d with |G| = %d", ps->shape, s->G);
+    bool tma = (B * (int)sizeof(VT)) % 16 == 0;
+    uint64_t n_reps_total = 0;
+    for (auto &p : parts) {
+        tma = tma && ((uintptr_t)p.x % 16) == 0;
+        n_reps_total += p.n_reps;
+    }
+    const char *gm = getenv("FTLM_HV_GATHER");
+    if (gm && strcmp(gm, "direct") == 0) tma = false;
+    ftlm_status st = hvp_choose_geom<VT>(plan.ops, a, tma, plan.geo);
+    if (st != FTLM_OK) return st;
+    uint64_t tiles = 0;
+    plan.tile0.clear();
+    plan.ntile.clear();
+    for (auto &p : parts) {
+        p.tile0 = tiles;
+        const uint64_t nt = (p.n_reps + plan.geo.tile_reps - 1) / plan.geo.tile_reps;
+        plan.tile0.push_back(tiles);
+        plan.ntile.push_back(nt);
+        tiles += nt;
+    }
+    plan.geo.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)plan.geo.grid, tiles));
+    a.n_parts = (int)parts.size();
+    a.n_tiles = tiles;
+    a.tile_reps = plan.geo.tile_reps;
+    a.nbuf = plan.geo.nbuf;
+    a.tma = plan.geo.tma;
+    a.rho_smem = plan.geo.rho_smem;
+    a.own = plan.geo.own;
+    if (getenv("FTLM_HV_VERBOSE"))
+        fprintf(stderr, "ftlm hvp plan: shape %d B %d warps %d nbuf %d tma %d rho_smem %d own %d grid %d tiles %llu "
+                        "tile_reps %d wait_limit %llu\n",
+                ps->shape, B, plan.geo.warps, plan.geo.nbuf, plan.geo.tma, plan.geo.rho_smem, plan.geo.own,
+                plan.geo.grid, (unsigned long long)tiles, plan.geo.tile_reps, (unsigned long long)a.wait_limit);
+    if (parts.size() == 1) a.part0 = parts[0];
+    a.parts = nullptr;
+    return FTLM_OK;
+}
+
+// Launch a plan (no host-device copies, so it can be captured in a graph).
+template <typename VT>
+ftlm_status hvp_launch_plan(const HvpPlan<VT> &plan, double *dot_part, cudaStream_t stream, bool timed) {
+    if (plan.a.n_tiles == 0) return FTLM_OK;
+    HvpArgs<VT> a = plan.a;
+    a.dot_part = dot_part;
+    if (a.n_parts > 1 && !a.parts) return fail(FTLM_EINVAL, "several parts need a device descriptor array");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed) hv_timer_begin(stream, &e0, &e1);
+    ftlm_status st = plan.ops->launch(a, plan.geo, stream);
+    if (timed) hv_timer_end(stream, e0, e1, plan.rows_total * (uint64_t)a.B);
+    return st;
+}
+
+template <typename VT>
+ftlm_status lift_impl(const ftlm_sector *s, const PackedSet *ps, const ftlm_basis *const *blocks, int B,
+                      VT *const *blk, VT *packed, int to_packed, cudaStream_t stream) {
+    LiftArgs la;
+    memset(&la, 0, sizeof(la));
+    la.n_reps = s->n_reps;
+    la.K = ps->K;
+    la.W = ps->W;
+    la.B = B;
+    la.to_packed = to_packed;
+    la.ntab = ps->d_ntab;
+    la.rec = ps->d_rec;
+    int z = 0;
+    for (int k = 0; k < ps->K; ++k) {
+        la.dims[k] = ps->dims[k];
+        la.zoff[k] = z;
+        z += ps->dims[k];
+        la.boff[k] = blocks[k]->d_off;
+        la.V[k] = sizeof(VT) == 8 ? (const void *)blocks[k]->d_V : (const void *)blocks[k]->d_Vf;
+        la.blk[k] = blk[k];
+    }
+    const uint64_t n = s->n_reps * (uint64_t)B;
+    if (n) {
+        count_launch();
+        lift_rows<VT><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(la, packed);
+        FTLM_CUDA(cudaGetLastError());
+    }
+    return FTLM_OK;
+}
+
+// One block through the packed kernel: lift x, H·v, lower y (stream-ordered scratch).
+template <typename VT>
+ftlm_status hv_block(const ftlm_basis *b, int B, const VT *x, VT *y, cudaStream_t stream) {
+    const PackedSet *ps = b->ps;
+    const size_t n = ps->rows * (size_t)B;
+    VT *xl = nullptr, *yl = nullptr;
+    FTLM_CUDA(cudaMallocAsync((void **)&xl, std::max<size_t>(n, 1) * sizeof(VT), stream));
+    cudaError_t e = cudaMallocAsync((void **)&yl, std::max<size_t>(n, 1) * sizeof(VT), stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(xl, stream);
+        return fail(e == cudaErrorMemoryAllocation ? FTLM_ENOMEM : FTLM_ECUDA, "H·v scratch: %s", cudaGetErrorString(e));
+    }
+    const ftlm_basis *one[1] = {b};
+    VT *xb[1] = {const_cast<VT *>(x)};
+    VT *yb[1] = {y};
+    ftlm_status st = lift_impl<VT>(b->sec, ps, one, B, xb, xl, 1, stream);
+    if (st == FTLM_OK) {
+        std::vector<HvpPart<VT>> parts(1);
+        hvp_part_of<VT>(b->sec, ps, one, xl, yl, parts[0]);
+        HvpPlan<VT> plan;
+        st = hvp_plan<VT>(b->sec, ps, parts, B, plan);
+        plan.rows_total = ps->rows;
+        if (st == FTLM_OK) st = hvp_launch_plan<VT>(plan, nullptr, stream, true);
+    }
+    if (st == FTLM_OK) st = lift_impl<VT>(b->sec, ps, one, B, yb, yl, 0, stream);
+    cudaFreeAsync(xl, stream);
+    cudaFreeAsync(yl, stream);
+    return st;
+}
+
+template <typename VT>
+ftlm_status hvp_run_one(const ftlm_sector *s, const PackedSet *ps, const ftlm_basis *const *blocks, int B, const VT *x,
+                        VT *y, cudaStream_t stream) {
+    std::vector<HvpPart<VT>> parts(1);
+    hvp_part_of<VT>(s, ps, blocks, x, y, parts[0]);
+    HvpPlan<VT> plan;
+    ftlm_status st = hvp_plan<VT>(s, ps, parts, B, plan);
+    if (st != FTLM_OK) return st;
+    plan.rows_total = ps->rows;
+    return hvp_launch_plan<VT>(plan, nullptr, stream, true);
+}
+
+template ftlm_status hvp_plan<float>(const ftlm_sector *, const PackedSet *, std::vector<HvpPart<float>> &, int,
+                                     HvpPlan<float> &);
+template ftlm_status hvp_plan<double>(const ftlm_sector *, const PackedSet *, std::vector<HvpPart<double>> &, int,
+                                      HvpPlan<double> &);
+template ftlm_status hvp_launch_plan<float>(const HvpPlan<float> &, double *, cudaStream_t, bool);
+template ftlm_status hvp_launch_plan<double>(const HvpPlan<double> &, double *, cudaStream_t, bool);
+template void hvp_part_of<float>(const ftlm_sector *, const PackedSet *, const ftlm_basis *const *, const float *,
+                                 float *, HvpPart<float> &);
+template void hvp_part_of<double>(const ftlm_sector *, const PackedSet *, const ftlm_basis *const *, const double *,
+                                  double *, HvpPart<double> &);
+
+template <typename VT>
+ftlm_status pack_impl(const ftlm_multiblock *mb, int B, VT *const *blk, VT *packed, int to_packed,
+                      cudaStream_t stream) {
+    ftlm_status st = lift_impl<VT>(mb->sec, mb->ps, mb->blocks.data(), B, blk, packed, to_packed, stream);
+    if (st != FTLM_OK) return st;
+    FTLM_CUDA(cudaStreamSynchronize(stream));
+    return FTLM_OK;
+}
+
+template ftlm_status lift_impl<float>(const ftlm_sector *, const PackedSet *, const ftlm_basis *const *, int,
+                                      float *const *, float *, int, cudaStream_t);
+template ftlm_status lift_impl<double>(const ftlm_sector *, const PackedSet *, const ftlm_basis *const *, int,
+                                       double *const *, double *, int, cudaStream_t);
+
+}  // namespace ftlm
+
+using namespace ftlm;
+
+extern "C" {
+
+ftlm_status ftlm_hv(const ftlm_basis *b, ftlm_dtype dtype, int B, const void *x, void *y, void *cuda_stream) {
+    if (!b || !x || !y) return fail(FTLM_EINVAL, "NULL argument");
+    if (B < 1 || B > kMaxB) return fail(FTLM_EINVAL, "B must be in 1..%d", kMaxB);
+    if (b->dim == 0) return FTLM_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (dtype == FTLM_F64) return hv_block<double>(b, B, (const double *)x, (double *)y, st);
+    if (dtype == FTLM_F32) return hv_block<float>(b, B, (const float *)x, (float *)y, st);
+    return fail(FTLM_EINVAL, "unknown dtype");
+}
+
+ftlm_status ftlm_multiblock_packed_rows(const ftlm_multiblock *mb, uint64_t *rows) {
+    if (!mb || !rows) return fail(FTLM_EINVAL, "NULL argument");
+    if (!mb->ps) return fail(FTLM_EUNSUPPORTED, "no packed layout for this block set");
+    *rows = mb->ps->rows;
+    return FTLM_OK;
+}
+
+ftlm_status ftlm_hv_packed(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, const void *x, void *y,
+                           void *cuda_stream) {
+    if (!mb || !x || !y) return fail(FTLM_EINVAL, "NULL argument");
+    if (B < 1 || B > kMaxB) return fail(FTLM_EINVAL, "B must be in 1..%d", kMaxB);
+    if (!mb->ps) return fail(FTLM_EUNSUPPORTED, "no packed layout for this block set");
+    if (mb->ps->rows == 0) return FTLM_OK;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const ftlm_basis *const *bl = mb->blocks.data();
+    if (dtype == FTLM_F64)
+        return hvp_run_one<double>(mb->sec, mb->ps, bl, B, (const double *)x, (double *)y, st);
+    if (dtype == FTLM_F32) return hvp_run_one<float>(mb->sec, mb->ps, bl, B, (const float *)x, (float *)y, st);
+    return fail(FTLM_EINVAL, "unknown dtype");
+}
+
+ftlm_status ftlm_multiblock_pack(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, const void *const *blocks,
+                                 void *packed, void *cuda_stream) {
+    if (!mb || !blocks || !packed) return fail(FTLM_EINVAL, "NULL argument");
+    if (B < 1 || B > kMaxB) return fail(FTLM_EINVAL, "B must be in 1..%d", kMaxB);
+    if (!mb->ps) return fail(FTLM_EUNSUPPORTED, "no packed layout for this block set");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (dtype == FTLM_F64) return pack_impl<double>(mb, B, (double *const *)blocks, (double *)packed, 1, st);
+    if (dtype == FTLM_F32) return pack_impl<float>(mb, B, (float *const *)blocks, (float *)packed, 1, st);
+    return fail(FTLM_EINVAL, "unknown dtype");
+}
+
+ftlm_status ftlm_multiblock_unpack(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, const void *packed,
+                                   void *const *blocks, void *cuda_stream) {
+    if (!mb || !blocks || !packed) return fail(FTLM_EINVAL, "NULL argument");
+    if (B < 1 || B > kMaxB) return fail(FTLM_EINVAL, "B must be in 1..%d", kMaxB);
+    if (!mb->ps) return fail(FTLM_EUNSUPPORTED, "no packed layout for this block set");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (dtype == FTLM_F64)
+        return pack_impl<double>(mb, B, (double *const *)blocks, const_cast<double *>((const double *)packed), 0, st);
+    if (dtype == FTLM_F32)
+        return pack_impl<float>(mb, B, (float *const *)blocks, const_cast<float *>((const float *)packed), 0, st);
+    return fail(FTLM_EINVAL, "unknown dtype");
+}
+
+ftlm_status ftlm_set_wait_limit(uint64_t cycles) {
+    g_wait_limit.store(cycles ? (unsigned long long)cycles : kDrainCycles);
+    return FTLM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,41 @@
+// Counter-based start vectors of the FTLM chains (Section 2.2: normalised
+// Gaussian random vectors; Rademacher +-1 for the batched configurations).
+// Philox4x32-10 of Salmon, Moraes, Dror and Shaw (SC'11), written from its
+// published definition: key (k0, k1), counter (c0, c1, c2, c3), ten rounds of
+// the two multiplications with the key schedule bumped by the Weyl constants.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include "ftlm.h"
+
+namespace ftlm {
+
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    }
+    return c;
+}
+
+__device__ __forceinline__ double start_value(uint64_t row, uint32_t chain, uint32_t k0, uint32_t k1, int rng) {
+    const U4 o = philox4x32_10(U4{(uint32_t)row, (uint32_t)(row >> 32), chain, 0u}, k0, k1);
+    if (rng == FTLM_RADEMACHER) return (o.x & 1u) ? -1.0 : 1.0;
+    const double u1 = ((double)(((uint64_t)(o.x >> 5) << 26) | (o.y >> 6)) + 0.5) * 0x1p-53;
+    const double u2 = (double)(((uint64_t)(o.z >> 5) << 26) | (o.w >> 6)) * 0x1p-53;
+    return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
+}
+
+}  // namespace ftlm

@@ -39,6 +39,14 @@ void hv_timer_end(cudaStream_t st, cudaEvent_t a, cudaEvent_t b, uint64_t rows) 
     g_pending.push_back({a, b, rows});
 }
 
+// H·v time measured elsewhere (events recorded inside a captured graph).
+void hv_profile_add(double ms, uint64_t rows) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_hv_ms += ms;
+    g_hv_rows += rows;
+    ++g_hv_launches;
+}
+
 }  // namespace ftlm
 
 using namespace ftlm;

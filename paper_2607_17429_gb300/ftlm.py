@@ -69,8 +69,16 @@ _SIGS = {
     "ftlm_multiblock_block": [_P, _I, _P],
     "ftlm_hv_multi": [_P, _I, _I, _P, _P, _P],
     "ftlm_lanczos_multi": [_P, _I, _I, _I, _U64, _P, _I, _P, _P, _P, _P],
+    "ftlm_lanczos_sets": [_I, _P, _I, _I, _I, _U64, _P, _I, _P, _P, _P, _P],
     "ftlm_thermo_noalloc": [_I, _I, _P, _P, _P, _P, _P, _I, _P, ctypes.c_double, _P, _P, _P],
     "ftlm_peak_probe": [_I, _U64, _I, _P, _P],
+    "ftlm_multiblock_packed_rows": [_P, _P],
+    "ftlm_multiblock_pack": [_P, _I, _I, _P, _P, _P],
+    "ftlm_multiblock_unpack": [_P, _I, _I, _P, _P, _P],
+    "ftlm_hv_packed": [_P, _I, _I, _P, _P, _P],
+    "ftlm_set_wait_limit": [_U64],
+    "ftlm_fill_label_keyed": [_P, _I, _I, _U64, _P, _P],
+    "ftlm_basis_rows": [_P, _I, _P, _P, _P, _P],
     "ftlm_profile_enable": [_I],
     "ftlm_profile_reset": [],
     "ftlm_profile_get": [_P],
@@ -319,6 +327,46 @@ def ftlm_hv_multi(mb: MultiBlock, dtype: int, B: int, xs, ys, stream=None) -> No
     _check(_lib.ftlm_hv_multi(mb.handle, dtype, B, xa, ya, _stream(stream)))
 
 
+def ftlm_multiblock_packed_rows(mb: MultiBlock) -> int:
+    r = _U64()
+    _check(_lib.ftlm_multiblock_packed_rows(mb.handle, ctypes.byref(r)))
+    return r.value
+
+
+def ftlm_multiblock_pack(mb: MultiBlock, dtype: int, B: int, blocks, packed, stream=None) -> None:
+    n = len(blocks)
+    arr = (ctypes.c_void_p * n)(*[_ptr(x) for x in blocks])
+    _check(_lib.ftlm_multiblock_pack(mb.handle, dtype, B, arr, _ptr(packed), _stream(stream)))
+
+
+def ftlm_multiblock_unpack(mb: MultiBlock, dtype: int, B: int, packed, blocks, stream=None) -> None:
+    n = len(blocks)
+    arr = (ctypes.c_void_p * n)(*[_ptr(x) for x in blocks])
+    _check(_lib.ftlm_multiblock_unpack(mb.handle, dtype, B, _ptr(packed), arr, _stream(stream)))
+
+
+def ftlm_hv_packed(mb: MultiBlock, dtype: int, B: int, x, y, stream=None) -> None:
+    _check(_lib.ftlm_hv_packed(mb.handle, dtype, B, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def ftlm_fill_label_keyed(b, dtype: int, B: int, seed: int, x, stream=None) -> None:
+    """x: device [dim][B] of the dtype; see include/ftlm.h for the definition of the entries."""
+    _check(_lib.ftlm_fill_label_keyed(b.handle, dtype, B, seed, _ptr(x), _stream(stream)))
+
+
+def ftlm_basis_rows(b, labels, stream=None):
+    """Packed labels -> (first block row or -1, n_Gamma) per label."""
+    lab = np.ascontiguousarray(labels, dtype=np.uint64)
+    first = np.zeros(len(lab), dtype=np.int64)
+    nrows = np.zeros(len(lab), dtype=np.int32)
+    _check(_lib.ftlm_basis_rows(b.handle, len(lab), _ptr(lab), _ptr(first), _ptr(nrows), _stream(stream)))
+    return first, nrows
+
+
+def ftlm_set_wait_limit(cycles: int) -> None:
+    _check(_lib.ftlm_set_wait_limit(int(cycles)))
+
+
 def ftlm_lanczos_multi(mb: MultiBlock, dtype: int, R: int, n_steps: int, seed: int, block_ids, rng: int = GAUSS,
                        stream=None):
     K = ftlm_multiblock_info(mb)["n_blocks"]
@@ -328,6 +376,21 @@ def ftlm_lanczos_multi(mb: MultiBlock, dtype: int, R: int, n_steps: int, seed: i
     steps = np.zeros((K, R), dtype=np.int32)
     _check(_lib.ftlm_lanczos_multi(mb.handle, dtype, R, n_steps, seed, _ptr(ids), rng, _stream(stream), _ptr(alpha),
                                    _ptr(beta), _ptr(steps)))
+    return alpha, beta, steps
+
+
+def ftlm_lanczos_sets(sets, dtype: int, R: int, n_steps: int, seed: int, block_ids, rng: int = GAUSS, stream=None):
+    """sets: list of MultiBlock with packed layouts; block_ids: [n_sets][K].  Returns alpha, beta
+    [n_sets][K][R][n_steps] and steps [n_sets][K][R]."""
+    n = len(sets)
+    K = ftlm_multiblock_info(sets[0])["n_blocks"]
+    arr = (ctypes.c_void_p * n)(*[m.handle for m in sets])
+    ids = np.ascontiguousarray(block_ids, dtype=np.uint64).reshape(n, K)
+    alpha = np.zeros((n, K, R, n_steps))
+    beta = np.zeros((n, K, R, n_steps))
+    steps = np.zeros((n, K, R), dtype=np.int32)
+    _check(_lib.ftlm_lanczos_sets(n, arr, dtype, R, n_steps, seed, _ptr(ids), rng, _stream(stream), _ptr(alpha),
+                                  _ptr(beta), _ptr(steps)))
     return alpha, beta, steps
 
 

@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 CASES = [("icosahedron", 1, 0), ("icosahedron", 1, 6), ("icosahedron", 1, 12), ("icosahedron", 3, 0),
          ("cuboctahedron", 1, 0), ("cuboctahedron", 2, 2), ("tetrahedron", 5, 2), ("ring:7", 1, 1),
          ("square:4x4", 1, 0), ("square:4x6", 1, 4), ("dodecahedron", 1, 0), ("dimer", 1, 0),
-         ("ring:6", 5, 0), ("cuboctahedron", 3, 12), ("icosahedron", 1, -4)]
+         ("ring:6", 5, 0), ("cuboctahedron", 3, 12), ("icosahedron", 1, -4),
+         ("cuboctahedron", 4, 32)]  # s = 2: 36-bit labels, most representatives above 2^32
 
 
 @pytest.mark.parametrize("name,two_s,two_M", CASES)

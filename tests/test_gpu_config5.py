@@ -1,0 +1,89 @@
+"""The largest single block at full size: s=3/2 dodecahedron, M = 0, irrep H_g.
+
+Sector dimension 86 981 744 944 (Table 1), block dimension 3 624 380 734
+(Table 2), 40-bit packed labels, 7.25e8 representatives.  The GPU basis and
+H·v are checked on sampled representatives: counts against Tables 1-2 and
+Burnside, sampled representatives against the oracle's orbit minimum, and
+sampled rows of H x (x label-keyed, so the oracle regenerates any row from its
+label without the 3.6e9-row table) against the oracle's rows (Eqs. 15-16), in
+FP32 and FP64.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import ftlm, product_group, torch_cuda
+from helpers import oracle_group, pack_labels
+from oracle import native
+from oracle.basis import hv_rows_by_label
+from workloads import cluster, label_keyed_values
+
+pytestmark = pytest.mark.gpu
+
+NAME, TWO_S, TWO_M = "dodecahedron", 3, 0
+D_HG = 3624380734  # Table 2
+
+
+def _golden_table2():
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "table2_dodecahedron_s32_M0.txt")
+    out = {}
+    for ln in open(path):
+        p = ln.split()
+        if len(p) == 4 and not ln.startswith("#"):
+            out[p[0]] = (int(p[1]), int(p[2]), int(p[3]))
+    return out
+
+
+def _sample_reps(og, n, seed):
+    """Random M = 0 states (digit sum 30 over 20 sites, digits 0..3) -> their orbit minima (base-4 labels)."""
+    rng = np.random.default_rng(seed)
+    reps = set()
+    while len(reps) < n:
+        dig = rng.integers(0, 4, og.n_sites)
+        if dig.sum() != (og.n_sites * TWO_S + TWO_M) // 2:
+            continue
+        lab = int(sum(int(v) * 4 ** k for k, v in enumerate(dig)))
+        reps.add(native.min_rep(og.n_sites, 4, og.perms, lab)[0])
+    return sorted(reps)
+
+
+def test_dodecahedron_s32_m0_hg_full_size():
+    torch = torch_cuda()
+    F = ftlm()
+    og = oracle_group(NAME)
+    c = cluster(NAME)
+    g = product_group(NAME)
+    sec = F.ftlm_build_sector(g, TWO_S, TWO_M)
+    info = F.ftlm_sector_info(sec)
+    assert info["sector_dim"] == 86981744944  # Table 1
+    inv = og.element(c.gens[2])
+    ir = [i for i, r in enumerate(og.irreps) if r.dim == 5 and r.chars[inv] > 0][0]  # H_g
+    blk = F.ftlm_build_block(sec, ir)
+    dim = F.ftlm_basis_info(blk)["dim"]
+    assert dim == D_HG == _golden_table2()["H_g"][2]
+    sample = _sample_reps(og, 200, 5)
+    first, nrows = F.ftlm_basis_rows(blk, pack_labels(sample, og.n_sites, TWO_S))
+    assert np.all(first >= 0)  # every sampled orbit minimum is in the table
+    B, seed = 1, 5
+    rows_ref = hv_rows_by_label(og, ir, c.bonds, 1.0, TWO_S, sample,
+                                lambda lab, n: label_keyed_values([lab], n, B, seed)[0])
+    for dt, tdt, tol in ((F.F32, torch.float32, 3e-5), (F.F64, torch.float64, 1e-12)):
+        x = torch.empty((dim, B), dtype=tdt, device="cuda")
+        F.ftlm_fill_label_keyed(blk, dt, B, seed, x)
+        y = torch.empty_like(x)
+        F.ftlm_hv(blk, dt, B, x, y)
+        F.ftlm_basis_check(blk)
+        del x
+        idx = torch.from_numpy(np.concatenate([np.arange(f, f + n) for f, n in zip(first, nrows)])).cuda()
+        got = y[idx].double().cpu().numpy()
+        del y
+        torch.cuda.empty_cache()
+        scale = max(np.abs(r).max() for r in rows_ref if r is not None)
+        pos = 0
+        for n, r in zip(nrows, rows_ref):
+            if n == 0:
+                assert r is None
+                continue
+            assert np.abs(got[pos:pos + n] - r).max() <= tol * scale
+            pos += n
