@@ -272,17 +272,21 @@ def hv_roofline(prof, dtype_name, flips, n_reps, W, B, esize):
 
     Algorithmic bytes = flips * (W*B*e + 20)   [every flipped state's segment, its record and bucket]
                       + n_reps * (2*W*B*e + 16) [the representative's own rows in, its outputs out, its record]
-    against the measured STREAM copy bandwidth (MEASURED_PEAKS.json hbm_gbs).
+    against the measured STREAM copy bandwidth (MEASURED_PEAKS.json hbm_gbs).  flips per launch is the
+    kernel's own device count while profiling (ftlm_profile.hv_flips), else the count from the labels.
     """
     pk, which = peaks()
     if prof["hv_launches"] == 0:
         return None
+    if prof.get("hv_flips"):
+        flips = prof["hv_flips"] / prof["hv_launches"]
     t = prof["hv_ms"] / prof["hv_launches"] / 1e3
     seg = W * B * esize
     byt = flips * (seg + 20) + n_reps * (2 * seg + 16)
     peak = float(pk["hbm_gbs"]) * 1e9
     return {"bound": "hbm", "achieved": byt / t / 1e9, "peak": peak / 1e9, "unit": "GB/s", "frac": byt / t / peak,
             "traffic": _traffic_record(dtype_name), "algorithmic_per_launch": byt, "avg_launch_ms": t * 1e3,
+            "flips_per_launch": flips,
             "peak_source": f"{which} MEASURED_PEAKS.json hbm_gbs" if which == "measured" else "fallback 6.8 TB/s",
             "kernel_sha": _kernel_sha()}
 
@@ -336,6 +340,323 @@ def cpu_baseline(budget_s=10.0):
                       f"processes x {busy:.1f} s (wall {wall:.1f} s including start-up)"}
 
 
+def hv_once():
+    """The profiling case: one packed H·v over all 10 blocks (FP32, B = 8) and one on the H_g block alone."""
+    import torch
+
+    from paper_2607_17429_gb300 import build as pb
+
+    pb.build()
+    from paper_2607_17429_gb300 import ftlm as F
+    from workloads import cluster
+
+    torch.cuda.set_device(0)
+    c = cluster(CLUSTER)
+    g = F.ftlm_group_init(c.gens, c.bonds)
+    sec = F.ftlm_build_sector(g, TWO_S, TWO_M)
+    mb = F.ftlm_build_multiblock(sec, list(range(10)))
+    rows = F.ftlm_multiblock_packed_rows(mb)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(0)
+    xp = torch.randn(rows, R, device="cuda", generator=gen)
+    yp = torch.empty_like(xp)
+    F.ftlm_hv_packed(mb, F.F32, R, xp, yp)
+    F.ftlm_basis_check(F.ftlm_multiblock_block(mb, 0))
+    del xp, yp
+    blk = F.ftlm_multiblock_block(mb, 8)
+    dim = F.ftlm_multiblock_info(mb)["dims"][8]
+    x = torch.randn(dim, R, device="cuda", generator=gen)
+    y = torch.empty_like(x)
+    F.ftlm_hv(blk, F.F32, R, x, y)
+    F.ftlm_basis_check(blk)
+    torch.cuda.synchronize()
+    print(json.dumps({"hv_once": "ok", "packed_rows": rows, "hg_dim": dim}))
+
+
+def config5(args):
+    """Largest single block: s=3/2 dodecahedron (N=20, I_h), M=0, H_g (3 624 380 734 states, Table 2),
+    R=1 Gaussian (seed 4), 60 Lanczos steps, FP32 vectors with FP64 alpha/beta, against an FP64 GPU run."""
+    import torch
+
+    from paper_2607_17429_gb300 import build as pb
+
+    pb.build()
+    from paper_2607_17429_gb300 import ftlm as F
+    from workloads import cluster
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    c = cluster("dodecahedron")
+    g = F.ftlm_group_init(c.gens, c.bonds)
+    info = F.ftlm_group_info(g)
+    _, perms = F.ftlm_group_irrep(g)
+    inv = int(np.nonzero((perms == c.gens[2]).all(axis=1))[0][0])
+    ir = [i for i, d in enumerate(info["dims"]) if d == 5 and info["chars"][i][inv] > 0][0]
+    out = {"metric": METRIC.replace("10 irrep blocks x 8 chains", "1 block x 1 chain"), "unit": "Gstates/s",
+           "config": {"workload": "dodecahedron s=3/2 M=0 H_g (D=3624380734), R=1 Gaussian (seed 4), 60 Lanczos "
+                      "steps", "cluster": "dodecahedron", "two_s": 3, "two_M": 0, "irrep": "H_g"}}
+    t0 = time.perf_counter()
+    sec = F.ftlm_build_sector(g, 3, 0, stream)
+    blk = F.ftlm_build_block(sec, ir, stream)
+    torch.cuda.synchronize()
+    out["build_s"] = time.perf_counter() - t0
+    dim = F.ftlm_basis_info(blk)["dim"]
+    out["dim"] = dim
+    out["n_reps"] = F.ftlm_sector_info(sec)["n_reps"]
+    res = {}
+    for name, dt in (("f32", F.F32), ("f64", F.F64)):
+        F.ftlm_profile_reset()
+        F.ftlm_profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        a, b, st = F.ftlm_lanczos(blk, dt, 1, N_STEPS, 4, 8, F.GAUSS, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        F.ftlm_profile_enable(False)
+        prof = F.ftlm_profile_get()
+        ms = e0.elapsed_time(e1)
+        th = F.ftlm_thermo([dict(two_M=0, d_gamma=5, dim=dim, alpha=a, beta=b, steps=st)], T_GRID, 1.0, stream)
+        res[name] = {"ms": ms, "steps": int(st[0]), "prof": prof, "thermo": th,
+                     "hv_ms_per_launch": prof["hv_ms"] / max(1, prof["hv_launches"])}
+    f32, f64 = res["f32"], res["f64"]
+    out["value"] = dim * f32["steps"] / (f32["ms"] / 1e3) / 1e9
+    out["ms_lanczos_f32"] = f32["ms"]
+    out["ms_lanczos_f64"] = f64["ms"]
+    out["hv_ms_per_launch_f32"] = f32["hv_ms_per_launch"]
+    out["hv_ms_per_launch_f64"] = f64["hv_ms_per_launch"]
+    out["roofline"] = hv_roofline(f32["prof"], "f32", 0, out["n_reps"], 5, 1, 4)
+    sel = T_GRID >= 0.05
+    a32, a64 = f32["thermo"], f64["thermo"]
+    out["E0_f32"], out["E0_f64"] = a32[4], a64[4]
+    out["mixed_vs_fp64"] = {"dE0_rel": abs(a32[4] - a64[4]) / abs(a64[4]),
+                            "max_dC_over_Cmax": float(np.abs(a32[2] - a64[2])[sel].max() / a64[2].max()),
+                            "max_dlnZ_rel": float(np.abs((a32[0] - a64[0]) / a64[0]).max()),
+                            "note": "one M = 0 block: C(T) of that block alone; chi is identically 0"}
+    print(json.dumps(out))
+
+
+CONFIG3 = [("cuboctahedron", 1), ("cuboctahedron", 2), ("icosahedron", 3)]
+
+
+def config3(args):
+    """Batched SpMM across uneven blocks: s=1/2 and s=1 cuboctahedron (O_h), s=3/2 icosahedron (I_h); every
+    M >= 0 sector x every irrep; R = 24 Rademacher vectors (seed 2), 60 steps, FP32 vectors with FP64
+    reductions.  Batched form: per cluster, all sectors as the parts of one launch per kernel, the step loop
+    in one CUDA graph, geometry from the autotuner.  Plain form: FP64, one block at a time."""
+    import torch
+
+    from paper_2607_17429_gb300 import build as pb
+
+    pb.build()
+    from paper_2607_17429_gb300 import ftlm as F
+    from workloads import cluster
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    R3, NL3, SEED3 = 24, 60, 2
+    F.ftlm_set_autotune(1)
+    out = {"metric": "FTLM blocks/h and Gstates/s, batched mixed vs plain FP64 (config 3)", "unit": "blocks/h",
+           "config": {"workload": "s=1/2 and s=1 cuboctahedron (O_h), s=3/2 icosahedron (I_h), all M>=0 x all "
+                      "irreps, R=24 Rademacher (seed 2), 60 Lanczos steps"}, "clusters": {}}
+    tot = {"blocks": 0, "states": 0, "ms_batched": 0.0, "ms_plain64": 0.0}
+    for name, two_s in CONFIG3:
+        c = cluster(name)
+        g = F.ftlm_group_init(c.gens, c.bonds)
+        info = F.ftlm_group_info(g)
+        n_ir = len(info["dims"])
+        N = c.n_sites
+        sets, ids, Ms = [], [], []
+        for two_M in range(N * two_s % 2, N * two_s + 1, 2):
+            sec = F.ftlm_build_sector(g, two_s, two_M, stream)
+            sets.append(F.ftlm_build_multiblock(sec, list(range(n_ir)), stream))
+            ids.append([64 * two_M + k for k in range(n_ir)])
+            Ms.append(two_M)
+        dims = [F.ftlm_multiblock_info(m)["dims"] for m in sets]
+        n_blocks = sum(1 for dd in dims for d in dd if d > 0)
+
+        def blocks_of(a, b, st):
+            return [dict(two_M=Ms[i], d_gamma=int(info["dims"][k]), dim=dims[i][k], alpha=a[i][k], beta=b[i][k],
+                         steps=st[i][k]) for i in range(len(sets)) for k in range(n_ir) if dims[i][k] > 0]
+
+        F.ftlm_lanczos_sets(sets, F.F32, R3, NL3, SEED3, ids, F.RADEMACHER, stream)  # warm-up (tuning)
+        torch.cuda.synchronize()
+        F.ftlm_profile_reset()
+        F.ftlm_profile_enable(True)
+        t0 = time.perf_counter()
+        a, b, st = F.ftlm_lanczos_sets(sets, F.F32, R3, NL3, SEED3, ids, F.RADEMACHER, stream)
+        torch.cuda.synchronize()
+        ms_b = (time.perf_counter() - t0) * 1e3
+        F.ftlm_profile_enable(False)
+        prof = F.ftlm_profile_get()
+        mixed = F.ftlm_thermo(blocks_of(a, b, st), T_GRID, 1.0, stream)
+        states = sum(dims[i][k] * int(st[i][k].sum()) for i in range(len(sets)) for k in range(n_ir))
+        # plain form: FP64, one block at a time
+        a64 = np.zeros_like(a)
+        b64 = np.zeros_like(b)
+        s64 = np.zeros_like(st)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, mb in enumerate(sets):
+            for k in range(n_ir):
+                if dims[i][k] == 0:
+                    continue
+                blk = F.ftlm_multiblock_block(mb, k)
+                a64[i][k], b64[i][k], s64[i][k] = F.ftlm_lanczos(blk, F.F64, R3, NL3, SEED3, ids[i][k], F.RADEMACHER,
+                                                                 stream)
+        torch.cuda.synchronize()
+        ms_p = (time.perf_counter() - t0) * 1e3
+        ref = F.ftlm_thermo(blocks_of(a64, b64, s64), T_GRID, 1.0, stream)
+        sel = T_GRID >= 0.05
+        out["clusters"][f"{name} 2s={two_s}"] = {
+            "sectors": len(sets), "blocks": n_blocks, "states_applied": states, "ms_batched_mixed": ms_b,
+            "ms_plain_fp64": ms_p, "hv_launches": prof["hv_launches"],
+            "hv_ms_per_launch": prof["hv_ms"] / max(1, prof["hv_launches"]),
+            "blocks_per_hour_batched": n_blocks / (ms_b / 1e3) * 3600, "blocks_per_hour_plain_fp64":
+            n_blocks / (ms_p / 1e3) * 3600,
+            "mixed_vs_fp64": {"dE0_rel": abs(mixed[4] - ref[4]) / abs(ref[4]),
+                              "max_dC_over_Cmax": float(np.abs(mixed[2] - ref[2])[sel].max() / ref[2].max()),
+                              "max_dchi_over_chimax": float(np.abs(mixed[3] - ref[3])[sel].max() / ref[3].max())}}
+        tot["blocks"] += n_blocks
+        tot["states"] += states
+        tot["ms_batched"] += ms_b
+        tot["ms_plain64"] += ms_p
+    out["value"] = tot["blocks"] / (tot["ms_batched"] / 1e3) * 3600
+    out["blocks_per_hour_plain_fp64"] = tot["blocks"] / (tot["ms_plain64"] / 1e3) * 3600
+    out["batched_mixed_over_plain_fp64"] = out["value"] / out["blocks_per_hour_plain_fp64"]
+    out["gstates_per_s_batched"] = tot["states"] / (tot["ms_batched"] / 1e3) / 1e9
+    out["autotune"] = F.ftlm_autotune_report()
+    print(json.dumps(out))
+
+
+CONFIG4 = [("icosahedron", 1), ("icosahedron", 5), ("square:4x4", 1), ("square:4x6", 1), ("cuboctahedron", 1)]
+
+
+def config4_jobs(F, groups, n_jobs=2000, rate=50.0, seed=3):
+    """The serving workload: Poisson arrivals at `rate` per second, each job uniform over the five systems,
+    then uniform over that system's M >= 0 sectors and its admissible irreps (real, d <= 5; one-dimensional
+    on the square lattices), R uniform over {1, 4, 24}, N_L uniform over 40..60."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_jobs))
+    jobs = []
+    for i in range(n_jobs):
+        sysi = int(rng.integers(len(CONFIG4)))
+        name, two_s = CONFIG4[sysi]
+        g, N, irreps = groups[sysi]
+        two_M = int(rng.choice(np.arange(N * two_s % 2, N * two_s + 1, 2)))
+        ir = int(rng.choice(irreps))
+        jobs.append(dict(t=float(t[i]), sys=sysi, name=name, two_s=two_s, two_M=two_M, irrep=ir,
+                         R=int(rng.choice([1, 4, 24])), n_steps=int(rng.integers(40, 61)), block_id=i))
+    return jobs
+
+
+def config4(args):
+    """Serving loop (config 4): 2000 FTLM jobs with Poisson arrivals at 50/s over five systems, admitted
+    under a 150 GB HBM cap with resident tables shared across jobs, FP32 vectors with FP64 reductions.
+    Reports p50/p99 latency (submission to completion), blocks/h and the plain-FP64 one-job-at-a-time rate
+    on a sample of the same jobs."""
+    import torch
+
+    from paper_2607_17429_gb300 import build as pb
+
+    pb.build()
+    from paper_2607_17429_gb300 import ftlm as F
+    from workloads import cluster
+
+    torch.cuda.set_device(0)
+    groups = []
+    for name, two_s in CONFIG4:
+        c = cluster(name)
+        g = F.ftlm_group_init(c.gens, c.bonds)
+        info = F.ftlm_group_info(g)
+        sq = name.startswith("square")
+        irreps = [k for k, (d, fs) in enumerate(zip(info["dims"], info["fs"]))
+                  if fs == 1 and d <= 5 and (d == 1 or not sq)]
+        groups.append((g, c.n_sites, irreps))
+    n_jobs = args.jobs
+    jobs = config4_jobs(F, groups, n_jobs=n_jobs)
+    cap = 150 << 30
+    srv = F.Server(cap_bytes=cap, n_workers=args.workers, max_parts=32)
+    ids = [None] * n_jobs
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i, j in enumerate(jobs):
+            dt = j["t"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            g = groups[j["sys"]][0]
+            ids[i] = srv.submit(g, j["two_s"], j["two_M"], j["irrep"], j["R"], j["n_steps"], 3, j["block_id"],
+                                F.GAUSS, F.F32)
+
+    th = threading.Thread(target=submitter)
+    t_start = time.perf_counter()
+    th.start()
+    lat, dims, states, empty, failed, fails = [], [], 0, 0, 0, {}
+    t_first, t_last = None, 0.0
+    for i in range(n_jobs):
+        while ids[i] is None:
+            time.sleep(0.001)
+        try:
+            info, a, b, st = srv.wait(ids[i])
+        except F.FtlmError as e:
+            failed += 1
+            j = jobs[i]
+            key = f"status {e.status}: {str(e).split(': ', 2)[-1][:120]}"
+            fails.setdefault(key, []).append(f"{j['name']} 2s={j['two_s']} 2M={j['two_M']} irrep={j['irrep']} "
+                                             f"R={j['R']}")
+            continue
+        lat.append(info["t_done"] - info["t_submit"])
+        t_first = info["t_submit"] if t_first is None else min(t_first, info["t_submit"])
+        t_last = max(t_last, info["t_done"])
+        if info["dim"] == 0:
+            empty += 1
+        dims.append(info["dim"])
+        states += int(info["dim"]) * int(st.sum())
+    th.join()
+    wall = time.perf_counter() - t_start
+    stats = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    makespan = t_last - t_first
+    done = len(lat) - empty
+    # plain FP64, one job at a time (tables built outside the timed calls), on a sample of the same jobs
+    sample = [j for j in jobs[: args.plain_sample]]
+    tables = {}
+    t_plain, n_plain = 0.0, 0
+    for j in sample:
+        key = (j["sys"], j["two_M"], j["irrep"])
+        if key not in tables:
+            tables[key] = F.ftlm_build_basis(groups[j["sys"]][0], j["two_s"], j["two_M"], j["irrep"])
+        blk = tables[key]
+        if F.ftlm_basis_info(blk)["dim"] == 0:
+            continue
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        F.ftlm_lanczos(blk, F.F64, j["R"], j["n_steps"], 3, j["block_id"], F.GAUSS)
+        t_plain += time.perf_counter() - t0
+        n_plain += 1
+    out = {"metric": "FTLM serving: p50/p99 job latency and blocks/h (config 4)", "unit": "blocks/h",
+           "config": {"workload": "2000 jobs, Poisson arrivals 50/s (seed 3), uniform over s=1/2 and s=5/2 "
+                      "icosahedron, 4x4 and 4x6 square lattices, s=1/2 cuboctahedron; random (M, Gamma), "
+                      "R in {1,4,24}, N_L in 40..60; 150 GB admission cap; FP32 vectors, FP64 reductions",
+                      "n_jobs": n_jobs, "workers": args.workers},
+           "value": done / makespan * 3600 if makespan > 0 else None,
+           "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                         "max": float(lat.max()), "mean": float(lat.mean())},
+           "jobs_done": int(len(lat)), "jobs_failed": failed,
+           "failures": {k: {"count": len(v), "first": v[:3]} for k, v in fails.items()},
+           "empty_blocks": empty, "makespan_s": makespan,
+           "wall_s": wall, "gstates_per_s": states / makespan / 1e9 if makespan > 0 else None,
+           "plain_fp64_one_at_a_time": {"jobs": n_plain, "s": t_plain,
+                                        "blocks_per_hour": n_plain / t_plain * 3600 if t_plain > 0 else None},
+           "server": {k: stats[k] for k in ("waves", "parts", "sectors_built", "sector_hits", "blocks_built",
+                                             "block_hits", "evictions", "peak_charged", "resident_table_bytes")}}
+    if t_plain > 0 and out["value"]:
+        out["served_mixed_over_plain_fp64"] = out["value"] / out["plain_fp64_one_at_a_time"]["blocks_per_hour"]
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,7 +666,30 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hv-once", action="store_true",
+                    help="one packed 10-block H·v and one H_g-block H·v of the workload, then exit (profiling case)")
+    ap.add_argument("--config5", action="store_true",
+                    help="the largest single block instead: s=3/2 dodecahedron, M=0, H_g (3.6e9 states), R=1")
+    ap.add_argument("--config4", action="store_true",
+                    help="serving loop: 2000 Poisson-arrival jobs over five systems under a 150 GB cap")
+    ap.add_argument("--jobs", type=int, default=2000)
+    ap.add_argument("--workers", type=int, default=3)
+    ap.add_argument("--plain-sample", type=int, default=200)
+    ap.add_argument("--config3", action="store_true",
+                    help="batched small blocks instead: every M>=0 sector x irrep of three clusters, R=24 Rademacher")
     args = ap.parse_args()
+    if args.hv_once:
+        hv_once()
+        return
+    if args.config5:
+        config5(args)
+        return
+    if args.config4:
+        config4(args)
+        return
+    if args.config3:
+        config3(args)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":

@@ -261,6 +261,23 @@ ftlm_status ftlm_hv_packed(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, c
                            void *cuda_stream);
 
 /*
+ * Autotuner of the packed H·v (no counterpart in the paper, which picks its
+ * batch width from free memory).  With on = 1, the first packed H·v plan of
+ * every (block shape, |G| class, label width, element type, B, gather path,
+ * log2 of the representative count) key times the candidate geometries on that
+ * plan's own vectors and keeps the fastest for the rest of the process: warps
+ * per CTA, staging buffers in flight, rho tables in shared memory or read
+ * through L1 (FP32), the own-row prefetch, representatives per tile.  Every
+ * candidate computes identical rows; only timing changes (Lanczos alpha/beta
+ * can change at the rounding level through the reduction tiling).  on = 0
+ * turns tuning off (the built-in choice, cached results kept); on = -1 also
+ * clears the cache.  ftlm_autotune_report writes one text line per cached key
+ * (choice, its time and the default's) into buf (len bytes, NUL-terminated).
+ */
+ftlm_status ftlm_set_autotune(int on);
+ftlm_status ftlm_autotune_report(char *buf, size_t len);
+
+/*
  * Cycle budget of every bounded device-side wait of the H·v kernels (the
  * mbarrier waits for bulk copies); 0 restores the default of 2^32 cycles
  * (about two seconds).  A wait that runs out records FTLM_ETIMEOUT, which
@@ -394,10 +411,16 @@ ftlm_status ftlm_thermo(int n_blocks, const ftlm_block *blocks, int n_T, const d
  * 2 x 2^19 doubles (8 MiB, held by every GPU that loads the library until the
  * process exits); n_chains * ld above 2^19 (or ld above 512) is rejected with
  * FTLM_EINVAL before any GPU work.  The call allocates nothing: no cudaMalloc,
- * cudaFree or allocating library routine.  The first call on each device
- * looks up the array's device address with that device current; make that
- * first call before any stream capture.  All calls share the one array and it
- * keeps the last call's contents; calls that overlap on the GPU (other
+ * cudaFree or allocating library routine.  The array itself is reserved by the
+ * CUDA driver when it loads the library's device code on a device: at library
+ * load with CUDA_MODULE_LOADING=EAGER, otherwise (CUDA's default, lazy
+ * loading) at the first use of that code on the device, which may be this
+ * call.  A call with n_chains = 0 (every other argument ignored) only makes
+ * the array and the call's kernels resident on the current device and returns
+ * FTLM_OK: make it before handing the rest of the device memory to a pool.
+ * The array's address is looked up on every call (valid after a context
+ * reset).  All calls share the one array and it keeps the last call's
+ * contents; calls that overlap on the GPU (other
  * streams, other host threads) race on it and must be serialised by the
  * caller.  Synchronises cuda_stream before returning; FTLM_EINTERNAL if a
  * chain's steps exceed ld or the eigensolve does not converge.
@@ -406,20 +429,91 @@ ftlm_status ftlm_thermo_noalloc(int n_chains, int ld, const int *m, const double
                                 const double *weight, const double *msq, int n_T, const double *T, double g,
                                 double *out, double *E0, void *cuda_stream);
 
+/* ---------------------------------------------------------------- serving loop */
+
+/*
+ * Serving loop for many independent FTLM jobs on one GPU.  The paper has no
+ * counterpart beyond choosing its batch width from free memory (Section 3);
+ * this is the continuous-batching form of ftlm_lanczos.
+ *
+ * A job is one block (2M, irrep) of a group's cluster at spin 2s with R
+ * chains (1..32) of n_steps (1..512) Lanczos steps, its own block_id (Philox
+ * key word 1, Section 2.2 reading C9) and the seed, generator and dtype of
+ * ftlm_lanczos.  The server owns a scheduler thread and n_workers worker
+ * threads, each with its own CUDA stream on the device current at creation.
+ *  - Admission: jobs are admitted in submission order while the device bytes
+ *    charged stay within cap_bytes.  Charged are the resident sector tables
+ *    (one per group, 2s, 2M; shared by every job on them), the resident
+ *    block tables (one per sector and irrep) and each admitted job's Lanczos
+ *    vectors and state (3 packed vectors of rows x min(R, 32) elements plus a
+ *    few MB).  A sector is estimated from its dimension before it is built and
+ *    charged its actual size after.  Tables that no admitted job references
+ *    are evicted least recently used first when room is needed.  A job that
+ *    does not fit even with nothing else admitted fails with FTLM_ENOMEM; a
+ *    job that would fit later waits (head of line).
+ *  - Waves: an idle worker takes the oldest admitted job and every admitted
+ *    job with the same group, 2s, irrep, R, dtype, rng and seed (up to
+ *    max_parts), and runs them as the parts of one packed Lanczos launch
+ *    (ftlm_lanczos_sets' machinery, S^z sectors may differ); each part stops
+ *    at its own n_steps.  A job's coefficients equal those of ftlm_lanczos on
+ *    the same block, seed and block_id up to rounding.
+ * The group must stay valid until every job submitted on it has finished.
+ * ftlm_server_submit validates the job and returns its id at once
+ * (FTLM_EINVAL for bad arguments).  ftlm_server_wait blocks until the job has
+ * finished (timeout_s < 0: no limit; FTLM_ETIMEOUT if it runs out, the job
+ * keeps running), fills info and the host arrays alpha/beta [R][n_steps] and
+ * steps_done [R] (any may be NULL), returns the job's status and forgets the
+ * job.  Times in info are seconds since the server was created.
+ * ftlm_server_free stops the threads after the waves in flight; jobs not yet
+ * started are dropped.
+ */
+typedef struct ftlm_server ftlm_server;
+typedef struct {
+    const ftlm_group *group;
+    int two_s, two_M, irrep;
+    int R, n_steps;
+    uint64_t seed, block_id;
+    ftlm_rng rng;
+    ftlm_dtype dtype;
+} ftlm_job;
+typedef struct {
+    ftlm_status status;
+    int d_gamma;
+    uint64_t dim;
+    double t_submit, t_admit, t_start, t_done;
+} ftlm_job_info;
+typedef struct {
+    uint64_t submitted, completed, failed, waves, parts;
+    uint64_t sectors_built, sector_hits, blocks_built, block_hits, evictions;
+    size_t cap, charged, peak_charged, resident_table_bytes;
+    int queued, ready, running_waves;
+} ftlm_server_stats;
+
+ftlm_status ftlm_server_create(size_t cap_bytes, int n_workers, int max_parts, ftlm_server **out);
+ftlm_status ftlm_server_submit(ftlm_server *srv, const ftlm_job *job, uint64_t *job_id);
+ftlm_status ftlm_server_wait(ftlm_server *srv, uint64_t job_id, double timeout_s, ftlm_job_info *info,
+                             double *alpha, double *beta, int *steps_done);
+ftlm_status ftlm_server_stats_get(ftlm_server *srv, ftlm_server_stats *out);
+void ftlm_server_free(ftlm_server *srv);
+
 /* ---------------------------------------------------------------- profiling */
 
 /*
  * Library-wide counters (tracing support; no counterpart in the paper beyond
  * its wall times).  kernel_launches counts every kernel the library launched
  * since the last reset.  While profiling is enabled, every H·v launch is
- * bracketed by CUDA events on its stream; hv_ms is their summed device time
- * and hv_rows the summed dim * B.  ftlm_profile_get waits for pending events.
+ * bracketed by CUDA events on its stream (events recorded inside the Lanczos
+ * graph for its launches); hv_ms is their summed device time, hv_rows the
+ * summed rows * B, and hv_flips the ladder flips (Eq. 3 terms) the packed
+ * H·v processed, counted on the device.  ftlm_profile_get waits for the
+ * device.
  */
 typedef struct {
     uint64_t kernel_launches;
     uint64_t hv_launches;
     double hv_ms;
     uint64_t hv_rows;
+    uint64_t hv_flips;
 } ftlm_profile;
 ftlm_status ftlm_profile_enable(int on);
 ftlm_status ftlm_profile_reset(void);

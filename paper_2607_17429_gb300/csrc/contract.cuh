@@ -1,15 +1,18 @@
 // Contraction of Eq. 15 for one flip and one right-hand side, specialised on the
 // irrep dimension D so that no predicated work is issued for D < 5.
 //
-// rho(g)^T tables are stored with padded rows: row length rho_row(D) elements
-// (1, 2, 4, 4, 8 for D = 1..5) so that a row is one or two 16-byte shared loads.
+// rho tables are stored with padded rows: row length rho_row(D) elements (1, 2,
+// 4, 4, 6 for D = 1..5), so that an FP32 row is one 16-byte load (D = 3, 4) or
+// three 8-byte loads (D = 5; an 8-byte shared load with a few distinct addresses
+// per warp takes one wavefront, a 16-byte load two), and an even-length row
+// holds the element pairs of the packed FP32 FMA.
 #pragma once
 
 #include "common.cuh"
 
 namespace ftlm {
 
-__host__ __device__ constexpr int rho_row(int D) { return D == 5 ? 8 : (D == 3 ? 4 : D); }
+__host__ __device__ constexpr int rho_row(int D) { return D == 5 ? 6 : (D == 3 ? 4 : D); }
 
 // elements of one padded table [G][D][rho_row(D)], rounded up to 16 bytes
 template <typename VT>
@@ -30,10 +33,13 @@ __device__ __forceinline__ void load_row(const VT *p, VT (&r)[RP]) {
             r[4 * i + 2] = v.z;
             r[4 * i + 3] = v.w;
         }
-    } else if constexpr (sizeof(VT) == 4 && RP == 2) {
-        const float2 v = reinterpret_cast<const float2 *>(p)[0];
-        r[0] = v.x;
-        r[1] = v.y;
+    } else if constexpr (sizeof(VT) == 4 && RP % 2 == 0) {
+#pragma unroll
+        for (int i = 0; i < RP / 2; ++i) {
+            const float2 v = reinterpret_cast<const float2 *>(p)[i];
+            r[2 * i] = v.x;
+            r[2 * i + 1] = v.y;
+        }
     } else if constexpr (sizeof(VT) == 8 && RP % 2 == 0) {
 #pragma unroll
         for (int i = 0; i < RP / 2; ++i) {

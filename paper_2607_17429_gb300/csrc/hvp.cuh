@@ -117,7 +117,7 @@ struct HvpArgs {
     const uint8_t *pos;      // general s: [kMaxG][64] bit position of site k after g
     const void *dtab;        // [n_bonds][kMaxG] XOR masks (s = 1/2) or signed deltas
     const uint8_t *bonds;    // [n_bonds][2]
-    const VT *rhoT;          // padded rho(g)^T tables of the K blocks, block k at rho_off[k]
+    const VT *rhoT;          // rho(g) of the K blocks, row-major with padded rows, block k at rho_off[k]
     int rho_total;
     int rho_off[kPMaxK];
     int n_parts;
@@ -133,6 +133,7 @@ struct HvpArgs {
     unsigned long long wait_limit;
     int *err;
     double *dot_part;        // [n_parts][gridDim.x][K][B] partial <x_k, y_k>, or null
+    unsigned long long *flips;  // profiling: ladder flips processed (one atomic per representative), or null
 };
 
 // ---------------------------------------------------------------- shared-memory layout
@@ -254,6 +255,66 @@ __device__ __forceinline__ void hvp_contract_block(const VT *__restrict__ R, con
 #pragma unroll
         for (int ga = 1; ga < D; ++ga) acc += row[ga] * u[ga];
         z[Z + be] += cf * acc;
+    }
+}
+
+// ---------------------------------------------------------------- contraction of one flip, one block
+
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+// two FP32 FMAs in one instruction (sm_100 and later): d = a * b + c, element-wise
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// z[beta] += cf * sum_gamma R[gamma * RP + beta] u[gamma] for beta < D.  FP32 with
+// D >= 2 runs pairs of output rows through fma.f32x2 (rows of R padded to RP,
+// an even count); otherwise scalar FMAs.  Same products and summation order
+// over gamma either way.
+template <typename VT, int D, int RP>
+__device__ __forceinline__ void hvp_rows(const VT *__restrict__ R, const VT (&u)[D], VT cf, VT *z) {
+    if constexpr (sizeof(VT) == 4 && D >= 2) {
+        constexpr int NP = (D + 1) / 2;
+        unsigned long long acc[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) acc[q] = 0ull;  // (+0.0f, +0.0f)
+#pragma unroll
+        for (int ga = 0; ga < D; ++ga) {
+            VT row[RP];
+            load_row<VT, RP>(R + ga * RP, row);
+            const unsigned long long uu = f2_pack(u[ga], u[ga]);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) acc[q] = f2_fma(f2_pack(row[2 * q], row[2 * q + 1]), uu, acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            float lo, hi;
+            f2_unpack(acc[q], lo, hi);
+            z[2 * q] += cf * lo;
+            if (2 * q + 1 < D) z[2 * q + 1] += cf * hi;
+        }
+    } else {
+        VT acc[D];
+#pragma unroll
+        for (int be = 0; be < D; ++be) acc[be] = (VT)0;
+#pragma unroll
+        for (int ga = 0; ga < D; ++ga) {
+            VT row[RP];
+            load_row<VT, RP>(R + ga * RP, row);
+#pragma unroll
+            for (int be = 0; be < D; ++be) acc[be] += row[be] * u[ga];
+        }
+#pragma unroll
+        for (int be = 0; be < D; ++be) z[be] += cf * acc[be];
     }
 }
 
@@ -379,7 +440,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
         const HvRec *rec = P.rec;
         const VT *sqrtS = P.sqrtS;
         const VT *__restrict__ x = P.x;
-        VT *y = P.y;
+        VT *__restrict__ y = P.y;
         for (uint64_t rep = r0 + wid; rep < r1 && !dead; rep += warps) {
             const HvRec rr = rec[rep];
             const int sid = (int)rr.sid;
@@ -389,6 +450,12 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                 continue;
             }
             const LT lab = (LT)rr.label;
+            if (!own_on) {  // the own rows are read in the epilogue: start bringing them into L2 now
+                const uint32_t bytes = (uint32_t)(W * B * (int)sizeof(VT));
+                const char *src = reinterpret_cast<const char *>(x + seg);
+                for (uint32_t o = (uint32_t)lane * 128u; o < bytes; o += 32u * 128u) prefetch_l2(src + o);
+                if (lane == 31) prefetch_l2(src + bytes - 1);  // the last line when the segment is not aligned
+            }
             if (own_on) {  // the representative's own rows (diagonal term, <x~, y~>) land during the search
                 fence_proxy_async_smem();
                 __syncwarp();
@@ -437,6 +504,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
             diag4 = __reduce_add_sync(kFullMask, diag4);
             const VT diag = a.J * (VT)diag4 * (VT)0.25;
             const int nf = __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]);
+            if (a.flips && lane == 0) atomicAdd(a.flips, (unsigned long long)nf);
 
             // 3-4. search and lookup, 32 flips per round; records to shared memory
             for (int base = 0; base < nf; base += 32) {
@@ -463,6 +531,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                 }
                 LT my_rp = 0;
                 int my_g = 0;
+#pragma unroll 2
                 for (int j = 0; j < nround; ++j) {
                     const int e = __shfl_sync(kFullMask, my_e, j);
                     const int sg = HALF ? 1 : __shfl_sync(kFullMask, my_sg, j);
@@ -592,19 +661,12 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                         constexpr int D = SH::template D<k>;
                         constexpr int Zk = SH::template Z<k>;
                         constexpr int RP = rho_row(D);
+                        // R[gamma][beta] = rho_k(g*)[gamma][beta]; z_beta += cf sum_gamma R[gamma][beta] u_gamma
                         const VT *R = rho_base + a.rho_off[k] + (size_t)g_j * D * RP;
                         VT u[D];
 #pragma unroll
                         for (int g2 = 0; g2 < D; ++g2) u[g2] = xs[(Zk + g2) * B];
-#pragma unroll
-                        for (int be = 0; be < D; ++be) {
-                            VT row[RP];
-                            load_row<VT, RP>(R + be * RP, row);
-                            VT acc = row[0] * u[0];
-#pragma unroll
-                            for (int ga = 1; ga < D; ++ga) acc += row[ga] * u[ga];
-                            z[Zk + be] += cf * acc;
-                        }
+                        hvp_rows<VT, D, RP>(R, u, cf, z + Zk);
                     });
                 }
                 __syncwarp();

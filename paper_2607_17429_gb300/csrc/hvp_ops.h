@@ -39,7 +39,7 @@ void hvp_part_of(const ftlm_sector *s, const PackedSet *ps, const ftlm_basis *co
                  HvpPart<VT> &p);
 template <typename VT>
 ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpPart<VT>> &parts, int B,
-                     HvpPlan<VT> &plan);
+                     HvpPlan<VT> &plan, cudaStream_t tune_stream);
 template <typename VT>
 ftlm_status hvp_launch_plan(const HvpPlan<VT> &plan, double *dot_part, cudaStream_t stream, bool timed);
 

@@ -18,6 +18,7 @@ constexpr int kMaxD = 5;        // irrep dimension supported on the GPU path
 constexpr int kMaxBonds = 64;   // bonds per cluster on the GPU path
 constexpr int kMaxB = 32;       // right-hand sides per H·v launch
 constexpr int kPMaxK = 10;      // blocks per packed set (compile-time shapes)
+constexpr int kMaxSteps = 512;  // Lanczos steps per chain
 
 // Record of one representative in a packed set: label, first row of its
 // segment in the packed vector, stabilizer subgroup id.
@@ -55,6 +56,7 @@ ftlm_status fail(ftlm_status st, const char *fmt, ...);
 void clear_error();
 void count_launch(int n = 1);
 bool profiling_on();
+unsigned long long *profile_flip_counter();
 
 struct Irrep {
     int dim = 0;

@@ -11,20 +11,12 @@
 #include <vector>
 
 #include "common.cuh"
+#include "lanczos_packed.h"
 #include "philox.cuh"
 #include "ritz_thermo.cuh"
 
 namespace ftlm {
 
-struct LzSetIn {
-    const ftlm_sector *sec;
-    const PackedSet *ps;
-    const ftlm_basis *const *blocks;
-    const uint64_t *block_ids;
-};
-template <typename VT>
-ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps, uint64_t seed, int rng,
-                           cudaStream_t stream, double *alpha, double *beta, int *steps_done);
 ftlm_status hv_multi_launch_f64(const ftlm_multiblock *mb, int B, const double *const *x, double *const *y,
                                cudaStream_t stream);
 ftlm_status hv_multi_launch_f32(const ftlm_multiblock *mb, int B, const float *const *x, float *const *y,

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "hvp_ops.h"
+#include "lanczos_packed.h"
 #include "philox.cuh"
 #include "ritz_thermo.cuh"
 
@@ -45,8 +46,7 @@ struct LzPart {
     const uint64_t *boff[kPMaxK];  // block k's row offsets [n_reps] (start-vector counters)
     uint32_t key1[kPMaxK];         // Philox key word 1 of block k (block id)
     int entry0;                    // index of (part, block 0, chain 0) in the state arrays: p * K * B
-    VT *y;                         // update: y in, w out; start vectors: output
-    const VT *u, *up;
+    VT *y;                         // start vectors: output
 };
 
 template <typename VT>
@@ -58,17 +58,16 @@ struct LzArgs {
     int tile_reps;
     int B, BT, lgBT;
     int dims[kPMaxK], zoff[kPMaxK];
-    int has_prev, rng;
+    int rng;
     uint32_t chain0, key0;
-    const VT *coef;        // [entries][3]: s_j, alpha_j s_j, beta_j s_{j-1}
     double *norm_part;     // [n_parts][gridDim.x][K][B]
 };
 
-// MODE 0: start vectors u_0 (Philox per block row index and chain, lifted by
-// V_k(r)); MODE 1: the update.  Both accumulate |.|^2 per (block, chain) and
-// write per-CTA partials.  Rows of representative r: r W + Z_k + gamma.
-template <typename VT, int K, int MODE>
-__global__ void __launch_bounds__(kLzThreads) lzp_kernel(const __grid_constant__ LzArgs<VT> a) {
+// Start vectors u_0 (Philox per block row index and chain, lifted by V_k(r)),
+// with |u_0|^2 per (block, chain) as per-CTA partials.  Rows of representative
+// r: r W + Z_k + gamma.
+template <typename VT, int K>
+__global__ void __launch_bounds__(kLzThreads) lzp_start(const __grid_constant__ LzArgs<VT> a) {
     __shared__ double red[kPMaxK * 32];
     const int warps = blockDim.x >> 5;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -80,9 +79,6 @@ __global__ void __launch_bounds__(kLzThreads) lzp_kernel(const __grid_constant__
     DotAcc<VT> acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k].zero();
-    VT cy[K], cu[K], cp[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) cy[k] = cu[k] = cp[k] = (VT)0;
     int cur = -1;
     auto flush = [&](int p) {
         double v[K];
@@ -125,15 +121,6 @@ __global__ void __launch_bounds__(kLzThreads) lzp_kernel(const __grid_constant__
         if (p != cur) {
             if (cur >= 0) flush(cur);
             cur = p;
-            if (MODE == 1 && b < B) {
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const VT *c = a.coef + ((size_t)P.entry0 + k * B + b) * 3;
-                    cy[k] = c[0];
-                    cu[k] = c[1];
-                    cp[k] = c[2];
-                }
-            }
         }
         const uint64_t r0 = (t - P.tile0) * (uint64_t)a.tile_reps;
         const uint64_t r1 = min(r0 + (uint64_t)a.tile_reps, P.n_reps);
@@ -146,32 +133,97 @@ __global__ void __launch_bounds__(kLzThreads) lzp_kernel(const __grid_constant__
                 const int D = a.dims[k];
                 for (int gam = fg; gam < D; gam += Q) {
                     const size_t e = ((size_t)rr.off + a.zoff[k] + gam) * B + b;
-                    if (MODE == 0) {
-                        const uint64_t row0 = __ldg(P.boff[k] + rep);
-                        VT v;
-                        if (sid == 0) {
-                            v = (VT)start_value(row0 + (uint64_t)gam, a.chain0 + (uint32_t)b, a.key0, P.key1[k], a.rng);
-                        } else {  // lift the n_k(r) coefficients: V_k(r) x_k(r)
-                            const int nk = __ldg(P.ntab + sid * K + k);
-                            const VT *Vr = P.V[k] + ((size_t)sid * D + gam) * D;
-                            v = (VT)0;
-                            for (int q = 0; q < nk; ++q)
-                                v += __ldg(Vr + q) *
-                                     (VT)start_value(row0 + (uint64_t)q, a.chain0 + (uint32_t)b, a.key0, P.key1[k], a.rng);
-                        }
-                        P.y[e] = v;
-                        acc[k].add(v, v);
-                    } else {
-                        VT w = cy[k] * P.y[e] - cu[k] * __ldg(P.u + e);
-                        if (a.has_prev) w -= cp[k] * __ldg(P.up + e);
-                        P.y[e] = w;
-                        acc[k].add(w, w);
+                    const uint64_t row0 = __ldg(P.boff[k] + rep);
+                    VT v;
+                    if (sid == 0) {
+                        v = (VT)start_value(row0 + (uint64_t)gam, a.chain0 + (uint32_t)b, a.key0, P.key1[k], a.rng);
+                    } else {  // lift the n_k(r) coefficients: V_k(r) x_k(r)
+                        const int nk = __ldg(P.ntab + sid * K + k);
+                        const VT *Vr = P.V[k] + ((size_t)sid * D + gam) * D;
+                        v = (VT)0;
+                        for (int q = 0; q < nk; ++q)
+                            v += __ldg(Vr + q) *
+                                 (VT)start_value(row0 + (uint64_t)q, a.chain0 + (uint32_t)b, a.key0, P.key1[k], a.rng);
                     }
+                    P.y[e] = v;
+                    acc[k].add(v, v);
                 }
             }
         }
     }
     if (cur >= 0) flush(cur);
+}
+
+// The update on the flat packed vector.  Rows of every representative are
+// consecutive W-row segments, so element e of a part has row (e / B) mod W and
+// chain e mod B; with a thread count that is a multiple of W * B every thread of
+// the grid-stride loop sees one fixed (row, chain), hence one block k, one set
+// of coefficients and one accumulator.  Parts are processed one after another;
+// per part every CTA writes its partial |w|^2 per (block, chain).
+template <typename VT>
+struct LzUpd {
+    int n_parts, W, B, K, has_prev;
+    int blk_of_row[32];         // block of each row of a segment
+    const uint64_t *elem0;      // [n_parts + 1] first element of each part in the vectors
+    const int *entry0;          // [n_parts] p * K * B
+    VT *y;                      // in: H u_j, out: w
+    const VT *u, *up;
+    const VT *coef;             // [entries][3]
+    double *norm_part;          // [n_parts][gridDim.x][K][B]
+};
+
+template <typename VT>
+__global__ void __launch_bounds__(kLzThreads) lzp_update(const __grid_constant__ LzUpd<VT> a) {
+    __shared__ double red[kLzThreads];
+    const int B = a.B, WB = a.W * a.B, K = a.K;
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int tb = (int)(g % (uint64_t)WB);
+    const int k = a.blk_of_row[tb / B], b = tb % B;
+    for (int p = 0; p < a.n_parts; ++p) {
+        const uint64_t e0 = a.elem0[p], n = a.elem0[p + 1] - e0;
+        const VT *c = a.coef + ((size_t)a.entry0[p] + k * B + b) * 3;
+        const VT cy = c[0], cu = c[1], cp = a.has_prev ? c[2] : (VT)0;
+        VT *y = a.y + e0;
+        const VT *u = a.u + e0;
+        const VT *up = a.up + e0;
+        DotAcc<VT> acc;
+        acc.zero();
+        uint64_t e = g;
+        for (; e + 3 * T < n; e += 4 * T) {  // four elements in flight per thread
+            VT yv[4], uv[4], pv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                yv[q] = y[e + q * T];
+                uv[q] = __ldg(u + e + q * T);
+                pv[q] = a.has_prev ? __ldg(up + e + q * T) : (VT)0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const VT w = cy * yv[q] - cu * uv[q] - cp * pv[q];
+                y[e + q * T] = w;
+                acc.add(w, w);
+            }
+        }
+        for (; e < n; e += T) {
+            const VT w = cy * y[e] - cu * __ldg(u + e) - (a.has_prev ? cp * __ldg(up + e) : (VT)0);
+            y[e] = w;
+            acc.add(w, w);
+        }
+        red[threadIdx.x] = acc.value();
+        __syncthreads();
+        if ((int)threadIdx.x < K * B) {  // fixed order over the CTA's threads
+            const int kk = threadIdx.x / B, bb = threadIdx.x % B;
+            const uint64_t gb = (uint64_t)blockIdx.x * blockDim.x;
+            double sum = 0.0;
+            for (int i = 0; i < (int)blockDim.x; ++i) {
+                const int tbi = (int)((gb + i) % (uint64_t)WB);
+                if (a.blk_of_row[tbi / B] == kk && tbi % B == bb) sum += red[i];
+            }
+            a.norm_part[((size_t)p * gridDim.x + blockIdx.x) * K * B + threadIdx.x] = sum;
+        }
+        __syncthreads();
+    }
 }
 
 struct LzState {
@@ -246,13 +298,13 @@ __global__ void lzp_finalize(int mode, int j, int K, int B, int grid, const uint
     }
 }
 
-template <typename VT, int MODE>
-ftlm_status lzp_launch(int K, const LzArgs<VT> &a, int grid, cudaStream_t st) {
+template <typename VT>
+ftlm_status lzp_start_launch(int K, const LzArgs<VT> &a, int grid, cudaStream_t st) {
     count_launch();
     switch (K) {
-        case 1: lzp_kernel<VT, 1, MODE><<<grid, kLzThreads, 0, st>>>(a); break;
-        case 5: lzp_kernel<VT, 5, MODE><<<grid, kLzThreads, 0, st>>>(a); break;
-        case 10: lzp_kernel<VT, 10, MODE><<<grid, kLzThreads, 0, st>>>(a); break;
+        case 1: lzp_start<VT, 1><<<grid, kLzThreads, 0, st>>>(a); break;
+        case 5: lzp_start<VT, 5><<<grid, kLzThreads, 0, st>>>(a); break;
+        case 10: lzp_start<VT, 10><<<grid, kLzThreads, 0, st>>>(a); break;
         default: return fail(FTLM_EUNSUPPORTED, "no recurrence kernel for %d blocks", K);
     }
     FTLM_CUDA(cudaGetLastError());
@@ -261,17 +313,6 @@ ftlm_status lzp_launch(int K, const LzArgs<VT> &a, int grid, cudaStream_t st) {
 
 }  // namespace
 
-// One packed set taking part in a Lanczos launch: sector, packed set, its K
-// blocks and their block ids (Philox key word 1).
-struct LzSetIn {
-    const ftlm_sector *sec;
-    const PackedSet *ps;
-    const ftlm_basis *const *blocks;
-    const uint64_t *block_ids;
-};
-
-// R chains on every block of every set, n_steps steps.  alpha, beta: host
-// [n_sets][K][R][n_steps]; steps_done: host [n_sets][K][R].
 template <typename VT>
 ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps, uint64_t seed, int rng,
                            cudaStream_t stream, double *alpha, double *beta, int *steps_done) {
@@ -288,7 +329,8 @@ ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps,
     for (int p = 0; p < P; ++p) {
         row0[p + 1] = row0[p] + sets[p].ps->rows;
         for (int k = 0; k < K; ++k) {
-            m_max[(size_t)p * K + k] = (int)std::min<uint64_t>((uint64_t)n_steps, sets[p].blocks[k]->dim);
+            const int lim = sets[p].n_steps > 0 ? std::min(sets[p].n_steps, n_steps) : n_steps;
+            m_max[(size_t)p * K + k] = (int)std::min<uint64_t>((uint64_t)lim, sets[p].blocks[k]->dim);
             m_all = std::max(m_all, m_max[(size_t)p * K + k]);
         }
     }
@@ -337,7 +379,7 @@ ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps,
             for (int p = 0; p < P; ++p)
                 hvp_part_of<VT>(sets[p].sec, sets[p].ps, sets[p].blocks, vb[q].p + row0[p] * B,
                                 vb[(q + 1) % 3].p + row0[p] * B, hparts[q][p]);
-            ftlm_status s0 = hvp_plan<VT>(sets[0].sec, ps0, hparts[q], B, plan[q]);
+            ftlm_status s0 = hvp_plan<VT>(sets[0].sec, ps0, hparts[q], B, plan[q], stream);
             if (s0 != FTLM_OK) return s0;
             plan[q].rows_total = rows;
             if (P > 1) {
@@ -367,65 +409,103 @@ ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps,
         const int lz_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(lz_tiles, (uint64_t)sms * 8));
         FTLM_CUDA(lz_part.alloc((size_t)P * lz_grid * K * B));
         FTLM_CUDA(cudaMemcpyAsync(tiles.p, tinfo.data(), tinfo.size() * 8, cudaMemcpyHostToDevice, stream));
-        std::vector<LzPart<VT>> lparts[4];  // rotations 0..2 (update) and 3 (start vectors)
-        DevBuf<LzPart<VT>> d_lparts[4];
-        LzArgs<VT> la[4];
-        for (int q = 0; q < 4; ++q) {
-            lparts[q].resize(P);
-            for (int p = 0; p < P; ++p) {
-                LzPart<VT> &lp = lparts[q][p];
-                memset(&lp, 0, sizeof(lp));
-                lp.n_reps = sets[p].sec->n_reps;
-                lp.tile0 = tinfo[2 * P + p];
-                lp.rec = sets[p].ps->d_rec;
-                lp.ntab = sets[p].ps->d_ntab;
-                for (int k = 0; k < K; ++k) {
-                    lp.V[k] = sizeof(VT) == 8 ? reinterpret_cast<const VT *>(sets[p].blocks[k]->d_V)
-                                              : reinterpret_cast<const VT *>(sets[p].blocks[k]->d_Vf);
-                    lp.boff[k] = sets[p].blocks[k]->d_off;
-                    lp.key1[k] = (uint32_t)sets[p].block_ids[k];
-                }
-                lp.entry0 = p * K * B;
-                if (q < 3) {  // step j with j % 3 == q: y = vb[(q+1)%3], u = vb[q], up = vb[(q+2)%3]
-                    lp.y = vb[(q + 1) % 3].p + row0[p] * B;
-                    lp.u = vb[q].p + row0[p] * B;
-                    lp.up = vb[(q + 2) % 3].p + row0[p] * B;
-                } else {
-                    lp.y = vb[0].p + row0[p] * B;
-                }
+        std::vector<LzPart<VT>> lparts(P);  // start vectors
+        DevBuf<LzPart<VT>> d_lparts;
+        LzArgs<VT> la;
+        for (int p = 0; p < P; ++p) {
+            LzPart<VT> &lp = lparts[p];
+            memset(&lp, 0, sizeof(lp));
+            lp.n_reps = sets[p].sec->n_reps;
+            lp.tile0 = tinfo[2 * P + p];
+            lp.rec = sets[p].ps->d_rec;
+            lp.ntab = sets[p].ps->d_ntab;
+            for (int k = 0; k < K; ++k) {
+                lp.V[k] = sizeof(VT) == 8 ? reinterpret_cast<const VT *>(sets[p].blocks[k]->d_V)
+                                          : reinterpret_cast<const VT *>(sets[p].blocks[k]->d_Vf);
+                lp.boff[k] = sets[p].blocks[k]->d_off;
+                lp.key1[k] = (uint32_t)sets[p].block_ids[k];
             }
-            LzArgs<VT> &A = la[q];
-            memset(&A, 0, sizeof(A));
-            A.n_parts = P;
-            if (P == 1) {
-                A.part0 = lparts[q][0];
-            } else {
-                FTLM_CUDA(d_lparts[q].alloc(P));
-                FTLM_CUDA(cudaMemcpyAsync(d_lparts[q].p, lparts[q].data(), P * sizeof(LzPart<VT>),
-                                          cudaMemcpyHostToDevice, stream));
-                A.parts = d_lparts[q].p;
-            }
-            A.n_tiles = lz_tiles;
-            A.tile_reps = lz_tile;
-            A.B = B;
-            A.BT = plan[0].a.BT;
-            A.lgBT = plan[0].a.lgBT;
+            lp.entry0 = p * K * B;
+            lp.y = vb[0].p + row0[p] * B;
+        }
+        memset(&la, 0, sizeof(la));
+        la.n_parts = P;
+        if (P == 1) {
+            la.part0 = lparts[0];
+        } else {
+            FTLM_CUDA(d_lparts.alloc(P));
+            FTLM_CUDA(cudaMemcpyAsync(d_lparts.p, lparts.data(), P * sizeof(LzPart<VT>), cudaMemcpyHostToDevice,
+                                      stream));
+            la.parts = d_lparts.p;
+        }
+        la.n_tiles = lz_tiles;
+        la.tile_reps = lz_tile;
+        la.B = B;
+        la.BT = plan[0].a.BT;
+        la.lgBT = plan[0].a.lgBT;
+        {
             int z = 0;
             for (int k = 0; k < K; ++k) {
-                A.dims[k] = ps0->dims[k];
-                A.zoff[k] = z;
+                la.dims[k] = ps0->dims[k];
+                la.zoff[k] = z;
                 z += ps0->dims[k];
             }
-            A.rng = rng;
-            A.chain0 = (uint32_t)chain0;
-            A.key0 = (uint32_t)seed;
-            A.coef = sizeof(VT) == 8 ? reinterpret_cast<const VT *>(st.coef64) : reinterpret_cast<const VT *>(st.coef32);
-            A.norm_part = lz_part.p;
-            A.has_prev = 0;
         }
+        la.rng = rng;
+        la.chain0 = (uint32_t)chain0;
+        la.key0 = (uint32_t)seed;
+        la.norm_part = lz_part.p;
         const uint64_t *hv_t0 = tiles.p, *hv_nt = tiles.p + P, *lz_t0 = tiles.p + 2 * P, *lz_nt = tiles.p + 3 * P;
+        // flat update: grid a multiple of W*B / gcd(W*B, threads) so every thread keeps one (row, chain)
+        const int WB = ps0->W * B;
+        int gg = WB, tt = kLzThreads;
+        while (tt) {
+            const int r = gg % tt;
+            gg = tt;
+            tt = r;
+        }
+        const int gstep = WB / gg;
+        const int up_grid = std::max(gstep, (sms * 8 + gstep - 1) / gstep * gstep);
+        DevBuf<double> up_part;
+        FTLM_CUDA(up_part.alloc((size_t)P * up_grid * K * B));
+        std::vector<uint64_t> elem0(P + 1), ut(2 * (size_t)P);
+        std::vector<int> ent(P);
+        for (int p = 0; p <= P; ++p) elem0[p] = row0[p] * (uint64_t)B;
+        for (int p = 0; p < P; ++p) {
+            ent[p] = p * K * B;
+            ut[p] = 0;
+            ut[P + p] = (uint64_t)up_grid;  // every CTA writes a partial of every part
+        }
+        DevBuf<uint64_t> d_elem0, d_ut;
+        DevBuf<int> d_ent;
+        FTLM_CUDA(d_elem0.alloc(P + 1));
+        FTLM_CUDA(d_ut.alloc(2 * (size_t)P));
+        FTLM_CUDA(d_ent.alloc(P));
+        FTLM_CUDA(cudaMemcpyAsync(d_elem0.p, elem0.data(), (P + 1) * 8, cudaMemcpyHostToDevice, stream));
+        FTLM_CUDA(cudaMemcpyAsync(d_ut.p, ut.data(), 2 * (size_t)P * 8, cudaMemcpyHostToDevice, stream));
+        FTLM_CUDA(cudaMemcpyAsync(d_ent.p, ent.data(), P * sizeof(int), cudaMemcpyHostToDevice, stream));
+        LzUpd<VT> ua[3];
+        for (int q = 0; q < 3; ++q) {
+            LzUpd<VT> &U = ua[q];
+            memset(&U, 0, sizeof(U));
+            U.n_parts = P;
+            U.W = ps0->W;
+            U.B = B;
+            U.K = K;
+            int r = 0;
+            for (int k = 0; k < K; ++k)
+                for (int d = 0; d < ps0->dims[k]; ++d) U.blk_of_row[r++] = k;
+            U.elem0 = d_elem0.p;
+            U.entry0 = d_ent.p;
+            U.y = vb[(q + 1) % 3].p;
+            U.u = vb[q].p;
+            U.up = vb[(q + 2) % 3].p;
+            U.coef = sizeof(VT) == 8 ? reinterpret_cast<const VT *>(st.coef64)
+                                     : reinterpret_cast<const VT *>(st.coef32);
+            U.norm_part = up_part.p;
+        }
         // ---- start vectors and their norms
-        ftlm_status s1 = lzp_launch<VT, 0>(K, la[3], lz_grid, stream);
+        ftlm_status s1 = lzp_start_launch<VT>(K, la, lz_grid, stream);
         if (s1 != FTLM_OK) return s1;
         count_launch();
         lzp_finalize<<<P, K * B, 0, stream>>>(0, 0, K, B, lz_grid, lz_t0, lz_nt, lz_part.p, st, tol);
@@ -453,16 +533,18 @@ ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps,
                 count_launch();
                 lzp_finalize<<<P, K * B, 0, ss>>>(1, j, K, B, hv_grid, hv_t0, hv_nt, hv_part.p, st, tol);
                 FTLM_CUDA(cudaGetLastError());
-                LzArgs<VT> A = la[q];
-                A.has_prev = j > 0;
-                s2 = lzp_launch<VT, 1>(K, A, lz_grid, ss);
-                if (s2 != FTLM_OK) return s2;
+                LzUpd<VT> U = ua[q];
+                U.has_prev = j > 0;
                 count_launch();
-                lzp_finalize<<<P, K * B, 0, ss>>>(2, j, K, B, lz_grid, lz_t0, lz_nt, lz_part.p, st, tol);
+                lzp_update<VT><<<up_grid, kLzThreads, 0, ss>>>(U);
+                FTLM_CUDA(cudaGetLastError());
+                count_launch();
+                lzp_finalize<<<P, K * B, 0, ss>>>(2, j, K, B, up_grid, d_ut.p, d_ut.p + P, up_part.p, st, tol);
                 FTLM_CUDA(cudaGetLastError());
             }
             return FTLM_OK;
         };
+        if (prof) profile_flip_counter();  // allocated before the capture (no allocation while capturing)
         if (use_graph) {
             cudaStream_t cap = nullptr;
             FTLM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));

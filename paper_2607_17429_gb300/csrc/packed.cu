@@ -11,9 +11,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <string>
+
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "hvp_ops.h"
@@ -167,7 +171,7 @@ ftlm_status packed_set_build(ftlm_sector *s, int K, const ftlm_basis *const *blo
         FTLM_CUDA(cudaMemcpy(ps->d_Pf[k], Pf.data(), Pf.size() * 4, cudaMemcpyHostToDevice));
         ps->device_bytes += Pm.size() * 12;
     }
-    // rho(g)^T tables of the blocks, concatenated (FP64 and FP32), padded rows as in contract.cuh
+    // rho(g) tables of the blocks, concatenated (FP64 and FP32), rows padded as in contract.cuh
     std::vector<double> rho;
     std::vector<float> rhof;
     const int G = s->G;
@@ -178,12 +182,12 @@ ftlm_status packed_set_build(ftlm_sector *s, int K, const ftlm_basis *const *blo
         ps->rho_offf[k] = (int)rhof.size();
         rho.resize(rho.size() + rho_table_elems<double>(G, d), 0.0);
         rhof.resize(rhof.size() + rho_table_elems<float>(G, d), 0.0f);
-        for (int g = 0; g < G; ++g)
-            for (int r = 0; r < d; ++r)
-                for (int c = 0; c < d; ++c) {
-                    const double v = ir.rho[((size_t)g * d + c) * d + r];
-                    rho[ps->rho_off[k] + ((size_t)g * d + r) * RP + c] = v;
-                    rhof[ps->rho_offf[k] + ((size_t)g * d + r) * RP + c] = (float)v;
+        for (int g = 0; g < G; ++g)  // rho(g) row-major, rows padded to RP: [g][gamma][beta]
+            for (int ga = 0; ga < d; ++ga)
+                for (int be = 0; be < d; ++be) {
+                    const double v = ir.rho[((size_t)g * d + ga) * d + be];
+                    rho[ps->rho_off[k] + ((size_t)g * d + ga) * RP + be] = v;
+                    rhof[ps->rho_offf[k] + ((size_t)g * d + ga) * RP + be] = (float)v;
                 }
     }
     ps->rho_total = (int)rho.size();
@@ -268,6 +272,20 @@ void hvp_fill_common(const ftlm_sector *s, const PackedSet *ps, int B, HvpArgs<V
     a.lgBT = lg;
     const int per16 = 16 / (int)sizeof(VT);
     a.slot_elems = (ps->W * B + per16 - 1) / per16 * per16;
+    // Pad the slot so that the Q flip groups' slots start in different bank windows: a contraction
+    // load reads word  fg * slot_words + row * B * esize/4 + b * esize/4  in every lane (fg, b), and the
+    // Q windows of bt * esize/4 words then tile the 32 banks (slot_words an odd multiple of the window;
+    // windows below 4 words keep the 16-byte slot alignment the bulk copies need).
+    {
+        const int ew = (int)sizeof(VT) / 4;
+        const int unit = std::max(4, bt * ew);
+        if (unit < 32)
+            for (int i = 0; i < 16; ++i) {
+                const int sw = a.slot_elems * ew;
+                if (sw % unit == 0 && (sw / unit) % 2 == 1) break;
+                a.slot_elems += per16;
+            }
+    }
     const int Q = 32 / bt;
     int st = Q * a.slot_elems;
     st = std::max(st, ps->W * bt);
@@ -345,13 +363,141 @@ ftlm_status hvp_choose_geom(const HvpOps<VT> *ops, HvpArgs<VT> a, bool tma, HvpG
     return fail(FTLM_EUNSUPPORTED, "packed H·v does not fit in shared memory");
 }
 
+// ---------------------------------------------------------------- autotuner
+//
+// With autotuning on, the first plan of every (shape, elements per lane, label
+// width, element type, B, gather path, log2 of the representative count) key
+// times the candidate geometries on the plan's own buffers and keeps the
+// fastest for the rest of the process: warps per CTA (the kernel's bound down
+// to 4), staging buffers in flight (1..4 on the bulk-copy path), rho tables in
+// shared memory or read through L1 (FP32), the own-row prefetch on or off, and
+// the representatives per tile (2, 4 or 8 per warp).  Every candidate computes
+// the same rows (one warp per representative, fixed flip order), so the choice
+// changes timing only.
+
+struct TuneKey {
+    int shape, gpl, half, vt, B, tma, lg;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(shape, gpl, half, vt, B, tma, lg) < std::tie(o.shape, o.gpl, o.half, o.vt, o.B, o.tma, o.lg);
+    }
+};
+struct TuneVal {
+    HvpGeom geo;
+    float ms, ms_default;
+    int tried;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tuned;
+std::atomic<int> g_autotune{0};
+
+template <typename VT>
+void hvp_retile(HvpPlan<VT> &plan, std::vector<HvpPart<VT>> &parts) {
+    uint64_t tiles = 0;
+    plan.tile0.clear();
+    plan.ntile.clear();
+    for (auto &p : parts) {
+        p.tile0 = tiles;
+        const uint64_t nt = (p.n_reps + plan.geo.tile_reps - 1) / plan.geo.tile_reps;
+        plan.tile0.push_back(tiles);
+        plan.ntile.push_back(nt);
+        tiles += nt;
+    }
+    plan.geo.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)plan.geo.grid, tiles));
+    HvpArgs<VT> &a = plan.a;
+    a.n_parts = (int)parts.size();
+    a.n_tiles = tiles;
+    a.tile_reps = plan.geo.tile_reps;
+    a.nbuf = plan.geo.nbuf;
+    a.tma = plan.geo.tma;
+    a.rho_smem = plan.geo.rho_smem;
+    a.own = plan.geo.own;
+    if (parts.size() == 1) a.part0 = parts[0];
+}
+
+template <typename VT>
+ftlm_status hvp_tune(HvpPlan<VT> &plan, std::vector<HvpPart<VT>> &parts, bool tma, cudaStream_t stream,
+                     TuneVal &out) {
+    int dev = 0, sms = kNumSMs;
+    FTLM_CUDA(cudaGetDevice(&dev));
+    FTLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    DevBuf<HvpPart<VT>> d_parts;
+    if (parts.size() > 1) FTLM_CUDA(d_parts.alloc(parts.size()));
+    cudaEvent_t e0, e1;
+    FTLM_CUDA(cudaEventCreate(&e0));
+    FTLM_CUDA(cudaEventCreate(&e1));
+    auto time_geo = [&](const HvpGeom &g, float &ms) -> ftlm_status {
+        plan.geo = g;
+        hvp_retile<VT>(plan, parts);
+        if (parts.size() > 1) {
+            FTLM_CUDA(cudaMemcpyAsync(d_parts.p, parts.data(), parts.size() * sizeof(HvpPart<VT>),
+                                      cudaMemcpyHostToDevice, stream));
+            plan.a.parts = d_parts.p;
+        }
+        ftlm_status st = hvp_launch_plan<VT>(plan, nullptr, stream, false);  // warm-up
+        if (st != FTLM_OK) return st;
+        FTLM_CUDA(cudaEventRecord(e0, stream));
+        st = hvp_launch_plan<VT>(plan, nullptr, stream, false);
+        if (st != FTLM_OK) return st;
+        FTLM_CUDA(cudaEventRecord(e1, stream));
+        FTLM_CUDA(cudaEventSynchronize(e1));
+        FTLM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return FTLM_OK;
+    };
+    const HvpGeom def = plan.geo;
+    float best_ms = 0.f;
+    ftlm_status st = time_geo(def, best_ms);
+    if (st != FTLM_OK) return st;
+    out.geo = def;
+    out.ms = out.ms_default = best_ms;
+    out.tried = 1;
+    const int max_warps = plan.ops->max_threads / 32;
+    std::vector<int> rho_opts = sizeof(VT) == 4 ? std::vector<int>{1, 0} : std::vector<int>{0};
+    std::vector<int> own_opts = tma ? std::vector<int>{0, 1} : std::vector<int>{0};
+    for (int warps = max_warps; warps >= 4; warps -= 4)
+        for (int rho : rho_opts)
+            for (int own : own_opts)
+                for (int nbuf = 1; nbuf <= (tma ? kMaxBuf : 1); ++nbuf)
+                    for (int tr : {2, 4, 8}) {
+                        HvpArgs<VT> a = plan.a;
+                        a.tma = tma ? 1 : 0;
+                        a.rho_smem = rho;
+                        a.own = own;
+                        const int per_sm = plan.ops->occupancy(a, warps, nbuf);
+                        if (per_sm < 1) continue;
+                        HvpGeom g{warps, nbuf, tma ? 1 : 0, warps * tr, sms * per_sm, rho, own};
+                        if (g.warps == def.warps && g.nbuf == def.nbuf && g.rho_smem == def.rho_smem &&
+                            g.own == def.own && g.tile_reps == def.tile_reps)
+                            continue;
+                        float ms = 0.f;
+                        if ((st = time_geo(g, ms)) != FTLM_OK) return st;
+                        ++out.tried;
+                        if (ms < out.ms) {
+                            out.ms = ms;
+                            out.geo = g;
+                        }
+                    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    plan.geo = out.geo;
+    plan.geo.grid = sms * std::max(1, plan.ops->occupancy([&] {
+                                           HvpArgs<VT> a = plan.a;
+                                           a.tma = out.geo.tma;
+                                           a.rho_smem = out.geo.rho_smem;
+                                           a.own = out.geo.own;
+                                           return a;
+                                       }(),
+                                                           out.geo.warps, out.geo.nbuf));
+    out.geo.grid = plan.geo.grid;
+    return FTLM_OK;
+}
+
 // Plan of a packed H·v launch over parts that share the set's shape and group:
 // arguments, geometry and tile order.  One part travels inside the kernel
 // arguments; several need a device array of descriptors (HvpPlan::a.parts),
 // filled by the caller before the launch and kept alive until it ends.
 template <typename VT>
 ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpPart<VT>> &parts, int B,
-                     HvpPlan<VT> &plan) {
+                     HvpPlan<VT> &plan, cudaStream_t tune_stream) {
     if (ps->shape < 0) return fail(FTLM_EUNSUPPORTED, "no compiled packed kernel for this block set");
     HvpArgs<VT> &a = plan.a;
     hvp_fill_common<VT>(s, ps, B, a);
@@ -369,30 +515,31 @@ ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpP
     if (gm && strcmp(gm, "direct") == 0) tma = false;
     ftlm_status st = hvp_choose_geom<VT>(plan.ops, a, tma, plan.geo);
     if (st != FTLM_OK) return st;
-    uint64_t tiles = 0;
-    plan.tile0.clear();
-    plan.ntile.clear();
-    for (auto &p : parts) {
-        p.tile0 = tiles;
-        const uint64_t nt = (p.n_reps + plan.geo.tile_reps - 1) / plan.geo.tile_reps;
-        plan.tile0.push_back(tiles);
-        plan.ntile.push_back(nt);
-        tiles += nt;
+    plan.rows_total = 0;
+    if (g_autotune.load() && !getenv("FTLM_HV_WARPS") && !getenv("FTLM_HV_NBUF")) {
+        int lg = 0;
+        while ((1ull << lg) < n_reps_total) ++lg;
+        const TuneKey key{ps->shape, gpl, s->half ? 1 : 0, (int)sizeof(VT), B, tma ? 1 : 0, lg};
+        std::unique_lock<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            plan.geo = it->second.geo;
+        } else {
+            lk.unlock();
+            TuneVal tv;
+            st = hvp_tune<VT>(plan, parts, tma, tune_stream, tv);
+            if (st != FTLM_OK) return st;
+            lk.lock();
+            g_tuned[key] = tv;
+        }
     }
-    plan.geo.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)plan.geo.grid, tiles));
-    a.n_parts = (int)parts.size();
-    a.n_tiles = tiles;
-    a.tile_reps = plan.geo.tile_reps;
-    a.nbuf = plan.geo.nbuf;
-    a.tma = plan.geo.tma;
-    a.rho_smem = plan.geo.rho_smem;
-    a.own = plan.geo.own;
+    hvp_retile<VT>(plan, parts);
+    const uint64_t tiles = a.n_tiles;
     if (getenv("FTLM_HV_VERBOSE"))
         fprintf(stderr, "ftlm hvp plan: shape %d B %d warps %d nbuf %d tma %d rho_smem %d own %d grid %d tiles %llu "
                         "tile_reps %d wait_limit %llu\n",
                 ps->shape, B, plan.geo.warps, plan.geo.nbuf, plan.geo.tma, plan.geo.rho_smem, plan.geo.own,
                 plan.geo.grid, (unsigned long long)tiles, plan.geo.tile_reps, (unsigned long long)a.wait_limit);
-    if (parts.size() == 1) a.part0 = parts[0];
     a.parts = nullptr;
     return FTLM_OK;
 }
@@ -403,6 +550,7 @@ ftlm_status hvp_launch_plan(const HvpPlan<VT> &plan, double *dot_part, cudaStrea
     if (plan.a.n_tiles == 0) return FTLM_OK;
     HvpArgs<VT> a = plan.a;
     a.dot_part = dot_part;
+    a.flips = profiling_on() ? profile_flip_counter() : nullptr;
     if (a.n_parts > 1 && !a.parts) return fail(FTLM_EINVAL, "several parts need a device descriptor array");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed) hv_timer_begin(stream, &e0, &e1);
@@ -461,7 +609,7 @@ ftlm_status hv_block(const ftlm_basis *b, int B, const VT *x, VT *y, cudaStream_
         std::vector<HvpPart<VT>> parts(1);
         hvp_part_of<VT>(b->sec, ps, one, xl, yl, parts[0]);
         HvpPlan<VT> plan;
-        st = hvp_plan<VT>(b->sec, ps, parts, B, plan);
+        st = hvp_plan<VT>(b->sec, ps, parts, B, plan, stream);
         plan.rows_total = ps->rows;
         if (st == FTLM_OK) st = hvp_launch_plan<VT>(plan, nullptr, stream, true);
     }
@@ -477,16 +625,16 @@ ftlm_status hvp_run_one(const ftlm_sector *s, const PackedSet *ps, const ftlm_ba
     std::vector<HvpPart<VT>> parts(1);
     hvp_part_of<VT>(s, ps, blocks, x, y, parts[0]);
     HvpPlan<VT> plan;
-    ftlm_status st = hvp_plan<VT>(s, ps, parts, B, plan);
+    ftlm_status st = hvp_plan<VT>(s, ps, parts, B, plan, stream);
     if (st != FTLM_OK) return st;
     plan.rows_total = ps->rows;
     return hvp_launch_plan<VT>(plan, nullptr, stream, true);
 }
 
 template ftlm_status hvp_plan<float>(const ftlm_sector *, const PackedSet *, std::vector<HvpPart<float>> &, int,
-                                     HvpPlan<float> &);
+                                     HvpPlan<float> &, cudaStream_t);
 template ftlm_status hvp_plan<double>(const ftlm_sector *, const PackedSet *, std::vector<HvpPart<double>> &, int,
-                                      HvpPlan<double> &);
+                                      HvpPlan<double> &, cudaStream_t);
 template ftlm_status hvp_launch_plan<float>(const HvpPlan<float> &, double *, cudaStream_t, bool);
 template ftlm_status hvp_launch_plan<double>(const HvpPlan<double> &, double *, cudaStream_t, bool);
 template void hvp_part_of<float>(const ftlm_sector *, const PackedSet *, const ftlm_basis *const *, const float *,
@@ -567,6 +715,35 @@ ftlm_status ftlm_multiblock_unpack(const ftlm_multiblock *mb, ftlm_dtype dtype, 
     if (dtype == FTLM_F32)
         return pack_impl<float>(mb, B, (float *const *)blocks, const_cast<float *>((const float *)packed), 0, st);
     return fail(FTLM_EINVAL, "unknown dtype");
+}
+
+ftlm_status ftlm_set_autotune(int on) {
+    g_autotune.store(on > 0 ? 1 : 0);
+    if (on < 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned.clear();
+    }
+    return FTLM_OK;
+}
+
+ftlm_status ftlm_autotune_report(char *buf, size_t len) {
+    if (!buf || len == 0) return fail(FTLM_EINVAL, "bad arguments");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    std::string s;
+    char line[256];
+    for (auto &kv : g_tuned) {
+        const TuneKey &k = kv.first;
+        const TuneVal &v = kv.second;
+        snprintf(line, sizeof line,
+                 "shape=%d gpl=%d half=%d esize=%d B=%d tma=%d log2reps=%d -> warps=%d nbuf=%d rho_smem=%d own=%d "
+                 "tile_reps=%d grid=%d ms=%.4f default_ms=%.4f tried=%d\n",
+                 k.shape, k.gpl, k.half, k.vt, k.B, k.tma, k.lg, v.geo.warps, v.geo.nbuf, v.geo.rho_smem, v.geo.own,
+                 v.geo.tile_reps, v.geo.grid, v.ms, v.ms_default, v.tried);
+        s += line;
+    }
+    if (s.size() + 1 > len) return fail(FTLM_EINVAL, "buffer of %zu bytes too small (%zu needed)", len, s.size() + 1);
+    memcpy(buf, s.c_str(), s.size() + 1);
+    return FTLM_OK;
 }
 
 ftlm_status ftlm_set_wait_limit(uint64_t cycles) {

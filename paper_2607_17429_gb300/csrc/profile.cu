@@ -17,7 +17,23 @@ struct Pending {
 std::vector<Pending> g_pending;
 uint64_t g_hv_launches = 0, g_hv_rows = 0;
 double g_hv_ms = 0.0;
+unsigned long long *g_flips[256] = {};  // per device: flip counter of the packed H·v
 }  // namespace
+
+// Device counter of ladder flips processed by the packed H·v while profiling
+// (allocated once per device on first use; null if that fails).
+unsigned long long *profile_flip_counter() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return nullptr;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_flips[dev]) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, sizeof(unsigned long long)) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, sizeof(unsigned long long));
+        g_flips[dev] = static_cast<unsigned long long *>(p);
+    }
+    return g_flips[dev];
+}
 
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 bool profiling_on() { return g_on.load(std::memory_order_relaxed) != 0; }
@@ -69,6 +85,11 @@ ftlm_status ftlm_profile_reset(void) {
     g_hv_launches = g_hv_rows = 0;
     g_hv_ms = 0.0;
     g_launches.store(0);
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 256 && g_flips[dev]) {
+        cudaDeviceSynchronize();
+        cudaMemset(g_flips[dev], 0, sizeof(unsigned long long));
+    }
     return FTLM_OK;
 }
 
@@ -90,6 +111,14 @@ ftlm_status ftlm_profile_get(ftlm_profile *out) {
     out->hv_launches = g_hv_launches;
     out->hv_ms = g_hv_ms;
     out->hv_rows = g_hv_rows;
+    out->hv_flips = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 256 && g_flips[dev]) {
+        unsigned long long f = 0;
+        FTLM_CUDA(cudaDeviceSynchronize());
+        FTLM_CUDA(cudaMemcpy(&f, g_flips[dev], sizeof(f), cudaMemcpyDeviceToHost));
+        out->hv_flips = f;
+    }
     return FTLM_OK;
 }
 

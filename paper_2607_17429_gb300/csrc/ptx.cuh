@@ -45,6 +45,10 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uin
                  : "memory");
 }
 
+// Hint to bring the 128-byte line holding p into L2; nothing to wait for, and
+// no effect on correctness.
+__device__ __forceinline__ void prefetch_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // One potentially blocking probe of the phase with the given parity (the
 // hardware may suspend the thread for a system-dependent time while the phase
 // is incomplete).

@@ -9,7 +9,6 @@
 
 namespace ftlm {
 
-constexpr int kMaxSteps = 512;
 constexpr int kThermoThreads = 256;
 
 // ---------------------------------------------------------------- tridiagonal eigensolve (implicit QL, FP64)

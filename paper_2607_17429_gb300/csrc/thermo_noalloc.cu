@@ -2,8 +2,6 @@
 // for callers that cannot allocate device memory.  Its only scratch, the
 // intermediate Ritz values and weights plus an error word, lives in one
 // file-scope device array of fixed size instead of cudaMalloc'd buffers.
-#include <mutex>
-
 #include "ritz_thermo.cuh"
 
 namespace ftlm {
@@ -15,24 +13,17 @@ constexpr size_t kNoAllocEntries = size_t(1) << 19;  // chains x steps held in t
 // loads the library holds this array until the process exits.
 static __device__ __align__(256) double g_thermo_scratch[2 * kNoAllocEntries + 32];
 
-std::mutex g_mu;
-double *g_scratch_addr[256] = {};
-
-// Device address of the scratch on the current device; looked up once per
-// device with that device current (host code cannot use the symbol itself).
+// Device address of the scratch in the current context.  Looked up on every
+// call, not cached: after a context reset (cudaDeviceReset) the module is
+// loaded again and the array may sit at another address.  Under lazy module
+// loading the first look-up on a device is what loads the module, and with it
+// reserves the array.
 ftlm_status scratch_on_current_device(double **out) {
-    int dev = -1;
-    FTLM_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 256) return fail(FTLM_EINVAL, "device index %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_thermo_scratch);
-        if (e != cudaSuccess || !p)
-            return fail(FTLM_ECUDA, "cudaGetSymbolAddress of the thermal scratch failed: %s", cudaGetErrorString(e));
-        g_scratch_addr[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_thermo_scratch);
+    if (e != cudaSuccess || !p)
+        return fail(FTLM_ECUDA, "cudaGetSymbolAddress of the thermal scratch failed: %s", cudaGetErrorString(e));
+    *out = static_cast<double *>(p);
     return FTLM_OK;
 }
 
@@ -44,6 +35,16 @@ using namespace ftlm;
 extern "C" ftlm_status ftlm_thermo_noalloc(int n_chains, int ld, const int *m, const double *alpha,
                                            const double *beta, const double *weight, const double *msq, int n_T,
                                            const double *T, double g, double *out, double *E0, void *cuda_stream) {
+    if (n_chains == 0) {  // warm-up: make the scratch and the three kernels resident on the current device
+        double *scr = nullptr;
+        ftlm_status st = scratch_on_current_device(&scr);
+        if (st != FTLM_OK) return st;
+        cudaFuncAttributes fa;  // under lazy loading, querying a kernel loads it
+        FTLM_CUDA(cudaFuncGetAttributes(&fa, ritz_kernel));
+        FTLM_CUDA(cudaFuncGetAttributes(&fa, ground_energy));
+        FTLM_CUDA(cudaFuncGetAttributes(&fa, thermo_kernel));
+        return FTLM_OK;
+    }
     if (n_chains < 1 || ld < 1 || n_T < 1 || !m || !alpha || !beta || !weight || !msq || !T || !out || !E0)
         return fail(FTLM_EINVAL, "bad arguments");
     if (ld > kMaxSteps) return fail(FTLM_EINVAL, "ld = %d exceeds %d steps", ld, kMaxSteps);

@@ -37,12 +37,30 @@ class FtlmError(RuntimeError):
 
 
 class ftlm_profile(ctypes.Structure):
-    _fields_ = [("kernel_launches", _U64), ("hv_launches", _U64), ("hv_ms", ctypes.c_double), ("hv_rows", _U64)]
+    _fields_ = [("kernel_launches", _U64), ("hv_launches", _U64), ("hv_ms", ctypes.c_double), ("hv_rows", _U64),
+                ("hv_flips", _U64)]
 
 
 class ftlm_block(ctypes.Structure):
     _fields_ = [("two_M", _I), ("d_gamma", _I), ("dim", _U64), ("R", _I), ("ld", _I),
                 ("steps_done", _P), ("alpha", _P), ("beta", _P)]
+
+
+class ftlm_job(ctypes.Structure):
+    _fields_ = [("group", _P), ("two_s", _I), ("two_M", _I), ("irrep", _I), ("R", _I), ("n_steps", _I),
+                ("seed", _U64), ("block_id", _U64), ("rng", _I), ("dtype", _I)]
+
+
+class ftlm_job_info(ctypes.Structure):
+    _fields_ = [("status", _I), ("d_gamma", _I), ("dim", _U64), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ftlm_server_stats(ctypes.Structure):
+    _fields_ = [(n, _U64) for n in ("submitted", "completed", "failed", "waves", "parts", "sectors_built",
+                                    "sector_hits", "blocks_built", "block_hits", "evictions")] + \
+               [(n, ctypes.c_size_t) for n in ("cap", "charged", "peak_charged", "resident_table_bytes")] + \
+               [(n, _I) for n in ("queued", "ready", "running_waves")]
 
 
 _SIGS = {
@@ -77,8 +95,14 @@ _SIGS = {
     "ftlm_multiblock_unpack": [_P, _I, _I, _P, _P, _P],
     "ftlm_hv_packed": [_P, _I, _I, _P, _P, _P],
     "ftlm_set_wait_limit": [_U64],
+    "ftlm_set_autotune": [_I],
+    "ftlm_autotune_report": [_P, ctypes.c_size_t],
     "ftlm_fill_label_keyed": [_P, _I, _I, _U64, _P, _P],
     "ftlm_basis_rows": [_P, _I, _P, _P, _P, _P],
+    "ftlm_server_create": [ctypes.c_size_t, _I, _I, _P],
+    "ftlm_server_submit": [_P, _P, _P],
+    "ftlm_server_wait": [_P, _U64, ctypes.c_double, _P, _P, _P, _P],
+    "ftlm_server_stats_get": [_P, _P],
     "ftlm_profile_enable": [_I],
     "ftlm_profile_reset": [],
     "ftlm_profile_get": [_P],
@@ -87,14 +111,14 @@ for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = ctypes.c_int
-for _name in ("ftlm_group_free", "ftlm_sector_free", "ftlm_basis_free", "ftlm_multiblock_free"):
+for _name in ("ftlm_group_free", "ftlm_sector_free", "ftlm_basis_free", "ftlm_multiblock_free", "ftlm_server_free"):
     getattr(_lib, _name).argtypes = [_P]
     getattr(_lib, _name).restype = None
 _lib.ftlm_last_error.restype = ctypes.c_char_p
 _lib.ftlm_last_error.argtypes = []
 
 EXPORTED = sorted(list(_SIGS) + ["ftlm_group_free", "ftlm_sector_free", "ftlm_basis_free", "ftlm_multiblock_free",
-                                  "ftlm_last_error"])
+                                  "ftlm_server_free", "ftlm_last_error"])
 
 
 def _check(st):
@@ -110,6 +134,28 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):  # torch tensor
         return a.data_ptr()
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev(a, dtype=None, numel=None, what="array"):
+    """Device address of a caller-owned array: a raw address (int, unchecked) or a CUDA tensor, checked to be
+    on a GPU, contiguous, of the element type (a torch dtype name, e.g. "float32") and at least numel long."""
+    if a is None or isinstance(a, int):
+        return a
+    if not hasattr(a, "data_ptr") or not hasattr(a, "is_cuda"):
+        raise TypeError(f"{what}: expected a CUDA tensor or a device address (int), got {type(a).__name__}")
+    if not a.is_cuda:
+        raise ValueError(f"{what}: tensor is on {a.device}, not on a CUDA device")
+    if not a.is_contiguous():
+        raise ValueError(f"{what}: tensor is not contiguous")
+    if dtype is not None and str(a.dtype) != "torch." + dtype:
+        raise TypeError(f"{what}: element type {a.dtype}, expected torch.{dtype}")
+    if numel is not None and a.numel() < numel:
+        raise ValueError(f"{what}: {a.numel()} elements, at least {numel} needed")
+    return a.data_ptr()
+
+
+def _vt(dtype):
+    return {F32: "float32", F64: "float64"}.get(dtype)
 
 
 def _stream(s):
@@ -322,8 +368,11 @@ def ftlm_multiblock_block(mb: MultiBlock, k: int):
 
 def ftlm_hv_multi(mb: MultiBlock, dtype: int, B: int, xs, ys, stream=None) -> None:
     n = len(xs)
-    xa = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
-    ya = (ctypes.c_void_p * n)(*[_ptr(y) for y in ys])
+    dims = ftlm_multiblock_info(mb)["dims"]
+    if len(ys) != n or n != len(dims):
+        raise ValueError(f"{len(dims)} blocks, got {n} inputs and {len(ys)} outputs")
+    xa = (ctypes.c_void_p * n)(*[_dev(x, _vt(dtype), d * B, f"x[{k}]") for k, (x, d) in enumerate(zip(xs, dims))])
+    ya = (ctypes.c_void_p * n)(*[_dev(y, _vt(dtype), d * B, f"y[{k}]") for k, (y, d) in enumerate(zip(ys, dims))])
     _check(_lib.ftlm_hv_multi(mb.handle, dtype, B, xa, ya, _stream(stream)))
 
 
@@ -333,25 +382,39 @@ def ftlm_multiblock_packed_rows(mb: MultiBlock) -> int:
     return r.value
 
 
-def ftlm_multiblock_pack(mb: MultiBlock, dtype: int, B: int, blocks, packed, stream=None) -> None:
+def _block_ptrs(mb, dtype, B, blocks):
+    dims = ftlm_multiblock_info(mb)["dims"]
+    if len(blocks) != len(dims):
+        raise ValueError(f"{len(dims)} blocks, got {len(blocks)} arrays")
     n = len(blocks)
-    arr = (ctypes.c_void_p * n)(*[_ptr(x) for x in blocks])
-    _check(_lib.ftlm_multiblock_pack(mb.handle, dtype, B, arr, _ptr(packed), _stream(stream)))
+    return (ctypes.c_void_p * n)(*[_dev(x, _vt(dtype), d * B, f"block[{k}]")
+                                   for k, (x, d) in enumerate(zip(blocks, dims))])
+
+
+def ftlm_multiblock_pack(mb: MultiBlock, dtype: int, B: int, blocks, packed, stream=None) -> None:
+    arr = _block_ptrs(mb, dtype, B, blocks)
+    rows = ftlm_multiblock_packed_rows(mb)
+    _check(_lib.ftlm_multiblock_pack(mb.handle, dtype, B, arr, _dev(packed, _vt(dtype), rows * B, "packed"),
+                                     _stream(stream)))
 
 
 def ftlm_multiblock_unpack(mb: MultiBlock, dtype: int, B: int, packed, blocks, stream=None) -> None:
-    n = len(blocks)
-    arr = (ctypes.c_void_p * n)(*[_ptr(x) for x in blocks])
-    _check(_lib.ftlm_multiblock_unpack(mb.handle, dtype, B, _ptr(packed), arr, _stream(stream)))
+    arr = _block_ptrs(mb, dtype, B, blocks)
+    rows = ftlm_multiblock_packed_rows(mb)
+    _check(_lib.ftlm_multiblock_unpack(mb.handle, dtype, B, _dev(packed, _vt(dtype), rows * B, "packed"), arr,
+                                       _stream(stream)))
 
 
 def ftlm_hv_packed(mb: MultiBlock, dtype: int, B: int, x, y, stream=None) -> None:
-    _check(_lib.ftlm_hv_packed(mb.handle, dtype, B, _ptr(x), _ptr(y), _stream(stream)))
+    n = ftlm_multiblock_packed_rows(mb) * B
+    _check(_lib.ftlm_hv_packed(mb.handle, dtype, B, _dev(x, _vt(dtype), n, "x"), _dev(y, _vt(dtype), n, "y"),
+                               _stream(stream)))
 
 
 def ftlm_fill_label_keyed(b, dtype: int, B: int, seed: int, x, stream=None) -> None:
     """x: device [dim][B] of the dtype; see include/ftlm.h for the definition of the entries."""
-    _check(_lib.ftlm_fill_label_keyed(b.handle, dtype, B, seed, _ptr(x), _stream(stream)))
+    n = ftlm_basis_info(b)["dim"] * B
+    _check(_lib.ftlm_fill_label_keyed(b.handle, dtype, B, seed, _dev(x, _vt(dtype), n, "x"), _stream(stream)))
 
 
 def ftlm_basis_rows(b, labels, stream=None):
@@ -361,6 +424,16 @@ def ftlm_basis_rows(b, labels, stream=None):
     nrows = np.zeros(len(lab), dtype=np.int32)
     _check(_lib.ftlm_basis_rows(b.handle, len(lab), _ptr(lab), _ptr(first), _ptr(nrows), _stream(stream)))
     return first, nrows
+
+
+def ftlm_set_autotune(on: int) -> None:
+    _check(_lib.ftlm_set_autotune(int(on)))
+
+
+def ftlm_autotune_report() -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(_lib.ftlm_autotune_report(buf, len(buf)))
+    return buf.value.decode()
 
 
 def ftlm_set_wait_limit(cycles: int) -> None:
@@ -399,7 +472,9 @@ def ftlm_lanczos_sets(sets, dtype: int, R: int, n_steps: int, seed: int, block_i
 
 def ftlm_hv(b: Basis, dtype: int, B: int, x, y, stream=None) -> None:
     """x, y: device pointers (int) or CUDA tensors of shape [dim, B] (float64 for F64, float32 for F32)."""
-    _check(_lib.ftlm_hv(b.handle, dtype, B, _ptr(x), _ptr(y), _stream(stream)))
+    n = ftlm_basis_info(b)["dim"] * B
+    _check(_lib.ftlm_hv(b.handle, dtype, B, _dev(x, _vt(dtype), n, "x"), _dev(y, _vt(dtype), n, "y"),
+                        _stream(stream)))
 
 
 def ftlm_lanczos(b: Basis, dtype: int, R: int, n_steps: int, seed: int, block_id: int, rng: int = GAUSS,
@@ -443,9 +518,65 @@ def ftlm_thermo(blocks, T, g=1.0, stream=None):
 
 
 def ftlm_thermo_noalloc(n_chains, ld, m, alpha, beta, weight, msq, n_T, T, g, out, E0, stream=None) -> None:
-    """All array arguments are device pointers (ints) or CUDA tensors; see include/ftlm.h."""
-    _check(_lib.ftlm_thermo_noalloc(int(n_chains), int(ld), _ptr(m), _ptr(alpha), _ptr(beta), _ptr(weight),
-                                    _ptr(msq), int(n_T), _ptr(T), float(g), _ptr(out), _ptr(E0), _stream(stream)))
+    """All array arguments are device addresses (ints) or CUDA tensors; see include/ftlm.h.  n_chains = 0 with
+    every array None only makes the library's fixed scratch resident on the current device."""
+    nc, nt = int(n_chains), int(n_T)
+    f = "float64"
+    _check(_lib.ftlm_thermo_noalloc(nc, int(ld), _dev(m, "int32", nc, "m"), _dev(alpha, f, nc * ld, "alpha"),
+                                    _dev(beta, f, nc * ld, "beta"), _dev(weight, f, nc, "weight"),
+                                    _dev(msq, f, nc, "msq"), nt, _dev(T, f, nt, "T"), float(g),
+                                    _dev(out, f, 4 * nt, "out"), _dev(E0, f, 1, "E0"), _stream(stream)))
+
+
+# ---------------------------------------------------------------- serving loop
+
+
+class Server:
+    """Serving loop (include/ftlm.h): submit jobs, wait for their alpha/beta.  Keeps the groups of
+    submitted jobs alive until the server is freed."""
+
+    def __init__(self, cap_bytes: int, n_workers: int = 2, max_parts: int = 64):
+        h = ctypes.c_void_p()
+        _check(_lib.ftlm_server_create(int(cap_bytes), int(n_workers), int(max_parts), ctypes.byref(h)))
+        self._h = h.value
+        self._groups = {}
+        self._shape = {}
+
+    def submit(self, group: Group, two_s: int, two_M: int, irrep: int, R: int, n_steps: int, seed: int,
+               block_id: int, rng: int = GAUSS, dtype: int = F32) -> int:
+        j = ftlm_job(group.handle, two_s, two_M, irrep, R, n_steps, seed, block_id, rng, dtype)
+        jid = _U64()
+        _check(_lib.ftlm_server_submit(self._h, ctypes.byref(j), ctypes.byref(jid)))
+        self._groups[id(group)] = group
+        self._shape[jid.value] = (R, n_steps)
+        return jid.value
+
+    def wait(self, job_id: int, timeout_s: float = -1.0):
+        """Returns (info dict, alpha [R][n_steps], beta, steps [R]); raises FtlmError with the job's status."""
+        R, n = self._shape[job_id]
+        info = ftlm_job_info()
+        alpha = np.zeros((R, n))
+        beta = np.zeros((R, n))
+        steps = np.zeros(R, dtype=np.int32)
+        st = _lib.ftlm_server_wait(self._h, job_id, float(timeout_s), ctypes.byref(info), _ptr(alpha), _ptr(beta),
+                                   _ptr(steps))
+        if st != ETIMEOUT:
+            self._shape.pop(job_id, None)
+        _check(st)
+        return ({f: getattr(info, f) for f, _ in ftlm_job_info._fields_}, alpha, beta, steps)
+
+    def stats(self) -> dict:
+        s = ftlm_server_stats()
+        _check(_lib.ftlm_server_stats_get(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in ftlm_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ftlm_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
 
 # ---------------------------------------------------------------- profiling
@@ -472,4 +603,5 @@ def ftlm_profile_reset() -> None:
 def ftlm_profile_get() -> dict:
     p = ftlm_profile()
     _check(_lib.ftlm_profile_get(ctypes.byref(p)))
-    return dict(kernel_launches=p.kernel_launches, hv_launches=p.hv_launches, hv_ms=p.hv_ms, hv_rows=p.hv_rows)
+    return dict(kernel_launches=p.kernel_launches, hv_launches=p.hv_launches, hv_ms=p.hv_ms, hv_rows=p.hv_rows,
+                hv_flips=p.hv_flips)

@@ -107,3 +107,37 @@ def test_error_paths(ftlm):
         ftlm.ftlm_group_set_irreps(g, [ir.rho for ir in og.irreps][:-1])  # incomplete
     assert e.value.status == ftlm.EIRREP
     assert "sum of d^2" in ftlm.ftlm_last_error()
+
+
+def test_binding_checks_device_arrays(ftlm):
+    """The binding passes a tensor's address only for a contiguous CUDA tensor of the right element type and
+    size; raw integer addresses pass unchecked (the C-ABI's contract)."""
+    torch = pytest.importorskip("torch")
+    x = torch.zeros(16, dtype=torch.float64)
+    with pytest.raises(ValueError, match="not on a CUDA device"):
+        ftlm._dev(x, "float64", 16, "x")
+    assert ftlm._dev(None) is None and ftlm._dev(12345) == 12345
+    with pytest.raises(TypeError, match="CUDA tensor or a device address"):
+        ftlm._dev(np.zeros(4), "float64", 4, "x")
+
+    class FakeCuda:  # stands in for a CUDA tensor on a machine without a GPU
+        def __init__(self, dtype, n, contiguous=True):
+            self.is_cuda, self.dtype, self.n, self.c = True, dtype, n, contiguous
+
+        def is_contiguous(self):
+            return self.c
+
+        def numel(self):
+            return self.n
+
+        def data_ptr(self):
+            return 4096
+
+    assert ftlm._dev(FakeCuda(torch.float32, 8), "float32", 8, "x") == 4096
+    with pytest.raises(TypeError, match="element type"):
+        ftlm._dev(FakeCuda(torch.float64, 8), "float32", 8, "x")
+    with pytest.raises(ValueError, match="at least 9"):
+        ftlm._dev(FakeCuda(torch.float32, 8), "float32", 9, "x")
+    with pytest.raises(ValueError, match="not contiguous"):
+        ftlm._dev(FakeCuda(torch.float32, 8, False), "float32", 8, "x")
+    assert ftlm._vt(ftlm.F32) == "float32" and ftlm._vt(ftlm.F64) == "float64"

@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 CASES = [("icosahedron", 1, 0), ("icosahedron", 1, 4), ("icosahedron", 3, 0), ("icosahedron", 3, 10),
          ("cuboctahedron", 1, 0), ("cuboctahedron", 2, 0), ("tetrahedron", 5, 2), ("ring:7", 1, 1),
          ("square:4x4", 1, 0), ("square:4x6", 1, 2), ("dodecahedron", 1, 0), ("ring:6", 5, 0),
-         ("cuboctahedron", 4, 32)]  # s = 2: 36-bit labels, most representatives above 2^32
+         ("cuboctahedron", 4, 32),  # s = 2: 36-bit labels, most representatives above 2^32
+         ("icosahedron", 5, 44)]  # s = 5/2: 3-bit fields, 36-bit labels
 
 _SECTORS = {}
 

@@ -227,3 +227,33 @@ def test_lanczos_sets_matches_each_set_alone(name, two_s):
         assert np.array_equal(st[i], s1)
         assert np.allclose(a[i], a1, rtol=1e-10, atol=1e-11)
         assert np.allclose(b[i], b1, rtol=1e-10, atol=1e-11)
+
+
+def test_autotune_changes_timing_only():
+    """The autotuner tries geometries on the plan's own vectors and keeps the fastest; every candidate
+    computes identical rows (one warp per representative, fixed flip order), so H·v is bitwise unchanged
+    and Lanczos coefficients agree to rounding."""
+    torch = torch_cuda()
+    F, og, sec, mb = _setup("icosahedron", 3, 2)
+    rows = F.ftlm_multiblock_packed_rows(mb)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1)
+    xp = torch.randn((rows, 8), dtype=torch.float32, device="cuda", generator=gen)
+    y0 = torch.empty_like(xp)
+    F.ftlm_hv_packed(mb, F.F32, 8, xp, y0)
+    a0, b0, s0 = F.ftlm_lanczos_multi(mb, F.F64, 4, 12, 3, list(range(10)))
+    F.ftlm_set_autotune(-1)
+    F.ftlm_set_autotune(1)
+    try:
+        y1 = torch.empty_like(xp)
+        F.ftlm_hv_packed(mb, F.F32, 8, xp, y1)
+        F.ftlm_basis_check(F.ftlm_multiblock_block(mb, 0))
+        a1, b1, s1 = F.ftlm_lanczos_multi(mb, F.F64, 4, 12, 3, list(range(10)))
+        report = F.ftlm_autotune_report()
+    finally:
+        F.ftlm_set_autotune(-1)
+        F.ftlm_set_autotune(0)
+    assert torch.equal(y0, y1)
+    assert np.array_equal(s0, s1)
+    assert np.allclose(a0, a1, rtol=1e-11, atol=1e-12) and np.allclose(b0, b1, rtol=1e-11, atol=1e-12)
+    assert "tried=" in report and len(report.strip().splitlines()) >= 2
