@@ -120,9 +120,12 @@ def run_ours(args, rank, world):
     n_ir = len(dims_g)
     ids = [64 * TWO_M + ir for ir in range(n_ir)]
 
-    def step_multi(grp, dt):
-        """Batched form: all 10 irrep blocks through one packed H·v launch per Lanczos step."""
+    def step_multi(grp, dt, flips=None):
+        """Batched form: all 10 irrep blocks through one packed H·v launch per Lanczos step; with the entry
+        table, the sector's flips are searched once per step and every H·v reads them."""
         sec = F.ftlm_build_sector(grp, TWO_S, TWO_M, stream)
+        if (flips or args.flips) == "table":
+            F.ftlm_sector_build_entries(sec, stream)
         mb = F.ftlm_build_multiblock(sec, list(range(n_ir)), stream)
         dims = F.ftlm_multiblock_info(mb)["dims"]
         a, b, st = F.ftlm_lanczos_multi(mb, dt, R, N_STEPS, SEED, ids, F.GAUSS, stream)
@@ -207,6 +210,14 @@ def run_ours(args, rank, world):
             "chi": "identically 0 in an M = 0-only run (chi needs M != 0 sectors)"}
         fp64["batched_mixed_over_plain_fp64_blocks_per_hour"] = (
             (n_ir * args.steps / (ms / 1e3)) / (n_ir / (fp64["plain_single_block"]["ms_per_step"] / 1e3)))
+        # FP16 storage (FP32 arithmetic, FP64 reductions), batched form, same seed
+        ms16, st16, prof16, out16 = timed(F.F16, 1, 1, step_multi)
+        res["fp16_storage"] = {
+            "value": st16 / (ms16 / 1e3) / 1e9, "unit": "Gstates/s", "ms_per_step": ms16,
+            "hv_ms_per_launch": prof16["hv_ms"] / max(1, prof16["hv_launches"]), "E0": out16[4],
+            "vs_fp64": {"dE0_rel": abs(out16[4] - ref[4]) / abs(ref[4]),
+                        "max_dC_over_Cmax": float(np.abs(out16[2] - ref[2])[sel].max() / ref[2].max()),
+                        "max_dlnZ_rel": float(np.abs((out16[0] - ref[0]) / ref[0]).max())}}
 
     # e2e: public API from host buffers, wall clock, copies inside
     torch.cuda.synchronize()
@@ -223,6 +234,12 @@ def run_ours(args, rank, world):
     res["e2e"] = {"value": e2e_states / t_e2e / 1e9, "unit": "Gstates/s", "h2d_bytes_per_step": int(h2d),
                   "d2h_bytes_per_step": int(d2h)}
     res["fp64"] = fp64
+    # the other flip path on the same workload (entry table vs on-the-fly search)
+    other = "search" if args.flips == "table" else "table"
+    ms_o, st_o, prof_o, out_o = timed(dtype, 1, 1, lambda grp, dt: step_multi(grp, dt, other))
+    res["other_flip_path"] = {"flips": other, "value": st_o / (ms_o / 1e3) / 1e9, "unit": "Gstates/s",
+                              "ms_per_step": ms_o, "hv_ms_per_launch": prof_o["hv_ms"] / max(1, prof_o["hv_launches"]),
+                              "dE0_vs_headline": abs(out_o[4] - out[4])}
     # measured rates of the box (context for the roofline)
     res["probes"] = {
         "gather_1KiB_GBs": F.ftlm_peak_probe(F.PEAK_GATHER, 2 << 30, 1024) / 1e9,
@@ -253,25 +270,27 @@ def _kernel_sha():
     return h.hexdigest()[:16]
 
 
-def _traffic_record(dtype_name):
+def _traffic_record(dtype_name, mode):
     """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
     sha = _kernel_sha()
     path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
     try:
         for ln in open(path):
             p = ln.split()
-            if len(p) >= 4 and p[0] == "hvp_kernel" and p[1] == dtype_name and p[3] == sha:
+            if len(p) >= 5 and p[0] == "hvp_kernel" and p[1] == dtype_name and p[3] == sha and p[4] == mode:
                 return float(p[2])
     except OSError:
         pass
     return None
 
 
-def hv_roofline(prof, dtype_name, flips, n_reps, W, B, esize):
+def hv_roofline(prof, dtype_name, flips, n_reps, W, B, esize, mode="search"):
     """Roofline of the dominant kernel (packed H·v), per launch, HBM bound.
 
-    Algorithmic bytes = flips * (W*B*e + 20)   [every flipped state's segment, its record and bucket]
-                      + n_reps * (2*W*B*e + 16) [the representative's own rows in, its outputs out, its record]
+    Search path:  flips * (W*B*e + 20)       [every flipped state's segment, its record and bucket]
+                + n_reps * (2*W*B*e + 16)    [the representative's own rows in, its outputs out, its record]
+    Table path:   flips * (W*B*e + 8)        [segment and 8-byte entry]
+                + n_reps * (2*W*B*e + 24)    [own rows, outputs, record and entry offset]
     against the measured STREAM copy bandwidth (MEASURED_PEAKS.json hbm_gbs).  flips per launch is the
     kernel's own device count while profiling (ftlm_profile.hv_flips), else the count from the labels.
     """
@@ -282,10 +301,14 @@ def hv_roofline(prof, dtype_name, flips, n_reps, W, B, esize):
         flips = prof["hv_flips"] / prof["hv_launches"]
     t = prof["hv_ms"] / prof["hv_launches"] / 1e3
     seg = W * B * esize
-    byt = flips * (seg + 20) + n_reps * (2 * seg + 16)
+    if mode == "table":
+        byt = flips * (seg + 8) + n_reps * (2 * seg + 24)
+    else:
+        byt = flips * (seg + 20) + n_reps * (2 * seg + 16)
     peak = float(pk["hbm_gbs"]) * 1e9
     return {"bound": "hbm", "achieved": byt / t / 1e9, "peak": peak / 1e9, "unit": "GB/s", "frac": byt / t / peak,
-            "traffic": _traffic_record(dtype_name), "algorithmic_per_launch": byt, "avg_launch_ms": t * 1e3,
+            "traffic": _traffic_record(dtype_name, mode), "algorithmic_per_launch": byt, "avg_launch_ms": t * 1e3,
+            "flip_path": mode,
             "flips_per_launch": flips,
             "peak_source": f"{which} MEASURED_PEAKS.json hbm_gbs" if which == "measured" else "fallback 6.8 TB/s",
             "kernel_sha": _kernel_sha()}
@@ -529,6 +552,9 @@ def config3(args):
     print(json.dumps(out))
 
 
+FLIP_PATHS = {"table": "entry table: one search pass per step (timed), then every H·v reads it",
+              "search": "representative search and lookup inside every H·v"}
+
 CONFIG4 = [("icosahedron", 1), ("icosahedron", 5), ("square:4x4", 1), ("square:4x6", 1), ("cuboctahedron", 1)]
 
 
@@ -666,6 +692,8 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--flips", default="table", choices=["table", "search"],
+                    help="entry table built once per step (the paper's two-phase design) or search in every H·v")
     ap.add_argument("--hv-once", action="store_true",
                     help="one packed 10-block H·v and one H_g-block H·v of the workload, then exit (profiling case)")
     ap.add_argument("--config5", action="store_true",
@@ -720,13 +748,14 @@ def main():
         return
     prof = res["prof"]
     esize = 4 if args.dtype == "f32" else 8
-    rl = hv_roofline(prof, args.dtype, res["flips"], res["n_reps"], res["W"], R, esize)
+    rl = hv_roofline(prof, args.dtype, res["flips"], res["n_reps"], res["W"], R, esize, args.flips)
     line = {
         "metric": METRIC, "value": res["value"], "unit": "Gstates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms_all"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
         "config": {"workload": WORKLOAD, "cluster": CLUSTER, "two_s": TWO_S, "two_M": TWO_M, "R": R,
-                   "lanczos_steps": N_STEPS, "blocks": len(res["dims"]), "precision": "FP32 vectors, FP64 alpha/beta"
+                   "lanczos_steps": N_STEPS, "blocks": len(res["dims"]), "flips": FLIP_PATHS[args.flips],
+                   "precision": "FP32 vectors, FP64 alpha/beta"
                    if args.dtype == "f32" else "FP64", "l2": "inputs larger than L2 (three packed [41.4M][8] "
                    "vectors of 1.3 GB each in FP32)", "parallelism": f"replicas{world}"},
         "blocks_per_hour": len(res["dims"]) * args.steps / (res["ms_all"] / 1e3) * 3600.0 * world,
@@ -738,6 +767,8 @@ def main():
         "e2e": res["e2e"],
         "clocks": res["clocks"],
         "fp64": res["fp64"],
+        "fp16_storage": res.get("fp16_storage"),
+        "other_flip_path": res.get("other_flip_path"),
         "probes": res["probes"],
     }
     if not args.no_cpu_baseline:

@@ -54,7 +54,12 @@ typedef enum {
     FTLM_EINTERNAL = 9     /* a device bounds check tripped (e.g. a representative missing from the table) */
 } ftlm_status;
 
-typedef enum { FTLM_F64 = 0, FTLM_F32 = 1 } ftlm_dtype; /* vector storage and H·v arithmetic */
+/* Vector storage and H·v arithmetic.  FTLM_F16: FP16 storage of the packed
+ * Lanczos vectors with FP32 arithmetic and FP64 reductions (Section 3's
+ * half-precision storage mode, with the per-block power-of-two scale of
+ * Section 4.2); offered by the packed entry points (ftlm_hv_packed and the
+ * Lanczos calls). */
+typedef enum { FTLM_F64 = 0, FTLM_F32 = 1, FTLM_F16 = 2 } ftlm_dtype;
 typedef enum { FTLM_GAUSS = 0, FTLM_RADEMACHER = 1 } ftlm_rng;
 
 typedef struct ftlm_group ftlm_group;   /* host: permutations, multiplication table, irreps, bonds */
@@ -137,6 +142,24 @@ ftlm_status ftlm_sector_info(const ftlm_sector *s, uint64_t *n_reps, uint64_t *s
 /* labels: [n_reps] packed labels; stab_mask: [n_reps][2] bit g of the 128-bit mask set when g fixes r. */
 ftlm_status ftlm_sector_export(const ftlm_sector *s, uint64_t *labels, uint64_t *stab_mask);
 void ftlm_sector_free(ftlm_sector *s);
+
+/*
+ * Entry table of a sector (Section 3: the two-phase design, where a
+ * preparation pass maps every ladder flip of every representative to its
+ * target representative and group element, and each H·v then reads the
+ * table instead of searching).  ftlm_sector_build_entries runs that pass once
+ * (the representative search and lookup of Eq. 15 for every flip of Eq. 3)
+ * and keeps the table on the device with the sector: 8 bytes per flip plus 8
+ * per representative, counted in ftlm_sector_info's device_bytes; n_entries
+ * (may be NULL) receives the flip count.  From then on every packed H·v and
+ * Lanczos call on blocks of this sector reads the table (the same flips in
+ * the same order as the search, so the results are bitwise those of the
+ * search path).  Synchronises cuda_stream; FTLM_ENOMEM if the table does not
+ * fit.  ftlm_sector_free_entries drops the table (back to the search).
+ * Neither may run while another call uses the sector.
+ */
+ftlm_status ftlm_sector_build_entries(const ftlm_sector *s, void *cuda_stream, uint64_t *n_entries);
+ftlm_status ftlm_sector_free_entries(const ftlm_sector *s);
 
 /*
  * Irrep-dependent preparation (Section 3's second phase): per stabilizer

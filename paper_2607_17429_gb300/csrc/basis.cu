@@ -223,6 +223,8 @@ void free_sector(ftlm_sector *s) {
     cudaFree(s->d_dtab);
     cudaFree(s->d_bonds);
     cudaFree(s->d_err);
+    cudaFree(s->d_eoff);
+    cudaFree(s->d_ent);
     delete s;
 }
 

@@ -38,6 +38,9 @@
 // while still taking part in the CTA barriers of the reductions.
 #pragma once
 
+#include <cuda_fp16.h>
+
+#include <mutex>
 #include <type_traits>
 #include <utility>
 
@@ -104,8 +107,10 @@ struct HvpPart {
     const uint8_t *wtab;     // [n_sid] sum over k of n_k(sid) (0: the orbit has no rows in the set)
     const VT *sqrtS;         // [n_sid]
     const VT *Pj[kPMaxK];    // block k: [n_sid][d_k][d_k] projector V V^T
-    const VT *x;             // lifted [n_reps * W][B]
-    VT *y;
+    const void *x;           // lifted [n_reps * W][B] of the storage type (VT, or FP16 with VT = float)
+    void *y;
+    const uint64_t *eoff;    // entry table of the sector ([n_reps + 1]; table and build modes)
+    HvEntry *ent;            // [n_entries] (read in table mode, written in build mode)
 };
 
 template <typename VT>
@@ -126,8 +131,9 @@ struct HvpArgs {
     uint64_t n_tiles;
     int tile_reps;
     int B, BT, lgBT, nbuf, tma;
-    int stage_elems;         // elements of one staging buffer
-    int slot_elems;          // elements of one flip's slot (W * B rounded up to 16 bytes)
+    int esize;               // bytes of one stored vector element (sizeof(VT), or 2 for FP16 storage)
+    int stage_elems;         // stored elements of one staging buffer
+    int slot_elems;          // stored elements of one flip's slot (W * B rounded up to 16 bytes, then padded)
     int rho_smem;            // FP32: rho tables staged in shared memory (else read through L1)
     int own;                 // bulk-copy path: prefetch the representative's own rows into shared memory
     unsigned long long wait_limit;
@@ -144,13 +150,14 @@ struct HvpLayout {
 
 template <typename VT, bool HALF>
 __host__ __device__ inline HvpLayout hvp_layout(int n_chunks, int n_bonds, int rho_total, int warps, int K, int W,
-                                                int B, int nbuf, int stage_elems, int own) {
+                                                int B, int nbuf, int stage_elems, int own, int esize,
+                                                bool search_tables = true) {
     constexpr int MAXF = HALF ? 64 : 128;
     HvpLayout L;
-    size_t o = HALF ? (size_t)n_chunks * 4 * kMaxG * 4 : (size_t)kMaxG * 64;
+    size_t o = !search_tables ? 0 : HALF ? (size_t)n_chunks * 4 * kMaxG * 4 : (size_t)kMaxG * 64;
     o = (o + 15) & ~(size_t)15;
     L.o_dtab = o;
-    o += (size_t)n_bonds * kMaxG * (HALF ? 4 : 8);
+    if (search_tables) o += (size_t)n_bonds * kMaxG * (HALF ? 4 : 8);
     o = (o + 15) & ~(size_t)15;
     L.o_rho = o;
     if (sizeof(VT) == 4) o += (size_t)rho_total * sizeof(VT);
@@ -170,8 +177,8 @@ __host__ __device__ inline HvpLayout hvp_layout(int n_chunks, int n_bonds, int r
     o += (size_t)warps * 8 * (kMaxBuf + 1);
     o = (o + 127) & ~(size_t)127;
     L.o_stage = o;  // per warp: nbuf staging buffers, then the representative's own rows
-    L.own_elems = own ? ((size_t)W * B * sizeof(VT) + 15) / 16 * 16 / sizeof(VT) : 0;
-    L.per_warp_stage = ((size_t)nbuf * stage_elems * sizeof(VT) + L.own_elems * sizeof(VT) + 127) & ~(size_t)127;
+    L.own_elems = own ? ((size_t)W * B * esize + 15) / 16 * 16 / esize : 0;
+    L.per_warp_stage = ((size_t)nbuf * stage_elems * esize + L.own_elems * esize + 127) & ~(size_t)127;
     o += (size_t)warps * L.per_warp_stage;
     L.total = o;
     return L;
@@ -318,6 +325,25 @@ __device__ __forceinline__ void hvp_rows(const VT *__restrict__ R, const VT (&u)
     }
 }
 
+// ---------------------------------------------------------------- storage conversions
+
+// Stored vector elements are VT, or FP16 for FP32 arithmetic (read widened to
+// FP32, written rounded to nearest).
+template <typename VT, typename ST>
+__device__ __forceinline__ VT st_get(ST v) {
+    if constexpr (std::is_same<ST, __half>::value)
+        return __half2float(v);
+    else
+        return (VT)v;
+}
+template <typename VT, typename ST>
+__device__ __forceinline__ ST st_put(VT v) {
+    if constexpr (std::is_same<ST, __half>::value)
+        return __float2half_rn(v);
+    else
+        return (ST)v;
+}
+
 // ---------------------------------------------------------------- the kernel
 
 // threads per CTA at most: 1024 for FP32 one-block shapes, fewer when registers are scarcer
@@ -326,7 +352,10 @@ __host__ __device__ constexpr int hvp_max_threads() {
     return (sizeof(VT) == 8 || SH::W > 8) ? 512 : 768;
 }
 
-template <typename VT, class SH, int GPL, bool HALF>
+// MODE 0: search (steps 1-4 on the fly); 1: table (flips read from the
+// sector's entry table, no images, search or lookup); 2: build (steps 1-4,
+// then the flips are written to the entry table; no gathers or outputs).
+template <typename VT, typename ST, class SH, int GPL, bool HALF, int MODE>
 __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const __grid_constant__ HvpArgs<VT> a) {
     using LT = typename std::conditional<HALF, uint32_t, uint64_t>::type;
     constexpr int K = SH::K;
@@ -337,9 +366,10 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
     const int wid = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const HvpLayout L = hvp_layout<VT, HALF>(a.n_chunks, a.n_bonds, a.rho_smem ? a.rho_total : 0, warps, K, W, a.B,
-                                             a.nbuf, a.stage_elems, a.tma && a.own);
-    const bool own_on = a.tma && a.own;
-    {
+                                             a.nbuf, a.stage_elems, MODE != 2 && a.tma && a.own, (int)sizeof(ST),
+                                             MODE != 1);
+    const bool own_on = MODE != 2 && a.tma && a.own;
+    if (MODE != 1) {
         const size_t n_tab = HALF ? (size_t)a.n_chunks * 4 * kMaxG * 4 : (size_t)kMaxG * 64;
         const uint4 *src0 = reinterpret_cast<const uint4 *>(HALF ? (const void *)a.lut2 : (const void *)a.pos);
         for (size_t i = threadIdx.x; i < n_tab / 16; i += blockDim.x) reinterpret_cast<uint4 *>(smem)[i] = src0[i];
@@ -347,6 +377,8 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
         const uint4 *src1 = reinterpret_cast<const uint4 *>(a.dtab);
         for (size_t i = threadIdx.x; i < n_dt / 16; i += blockDim.x)
             reinterpret_cast<uint4 *>(smem + L.o_dtab)[i] = src1[i];
+    }
+    {
         if (a.rho_smem) {
             const uint4 *src2 = reinterpret_cast<const uint4 *>(a.rhoT);
             for (int i = threadIdx.x; i < a.rho_total * (int)sizeof(VT) / 16; i += blockDim.x)
@@ -371,9 +403,9 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
     VT *f_c = reinterpret_cast<VT *>(smem + L.o_fc) + (size_t)wid * MAXF;
     const uint32_t bar0 = smem_u32(smem + L.o_bar + 8 * (kMaxBuf + 1) * wid);
     const uint32_t bar_own = bar0 + 8 * kMaxBuf;
-    VT *stage = reinterpret_cast<VT *>(smem + L.o_stage + (size_t)wid * L.per_warp_stage);
+    ST *stage = reinterpret_cast<ST *>(smem + L.o_stage + (size_t)wid * L.per_warp_stage);
     const uint32_t stage_s = smem_u32(stage);
-    VT *own = stage + (size_t)a.nbuf * a.stage_elems;  // the representative's own rows (bulk-copy path)
+    ST *own = stage + (size_t)a.nbuf * a.stage_elems;  // the representative's own rows (bulk-copy path)
     const uint32_t own_s = smem_u32(own);
 
     const int B = a.B, BT = a.BT;
@@ -439,19 +471,19 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
         const uint64_t r1 = min(r0 + (uint64_t)a.tile_reps, n_reps);
         const HvRec *rec = P.rec;
         const VT *sqrtS = P.sqrtS;
-        const VT *__restrict__ x = P.x;
-        VT *__restrict__ y = P.y;
+        const ST *__restrict__ x = static_cast<const ST *>(P.x);
+        ST *__restrict__ y = static_cast<ST *>(P.y);
         for (uint64_t rep = r0 + wid; rep < r1 && !dead; rep += warps) {
             const HvRec rr = rec[rep];
             const int sid = (int)rr.sid;
             const size_t seg = (size_t)rr.off * B;  // first element of r's W rows
-            if (sid != 0 && __ldg(P.wtab + sid) == 0) {  // no block has rows for this orbit: y~(r) = 0
-                for (int e = lane; e < W * B; e += 32) y[seg + e] = (VT)0;
+            if (MODE != 2 && sid != 0 && __ldg(P.wtab + sid) == 0) {  // no block has rows for this orbit: y~(r) = 0
+                for (int e = lane; e < W * B; e += 32) y[seg + e] = st_put<VT, ST>((VT)0);
                 continue;
             }
             const LT lab = (LT)rr.label;
-            if (!own_on) {  // the own rows are read in the epilogue: start bringing them into L2 now
-                const uint32_t bytes = (uint32_t)(W * B * (int)sizeof(VT));
+            if (MODE != 2 && !own_on) {  // the own rows are read in the epilogue: start bringing them into L2 now
+                const uint32_t bytes = (uint32_t)(W * B * (int)sizeof(ST));
                 const char *src = reinterpret_cast<const char *>(x + seg);
                 for (uint32_t o = (uint32_t)lane * 128u; o < bytes; o += 32u * 128u) prefetch_l2(src + o);
                 if (lane == 31) prefetch_l2(src + bytes - 1);  // the last line when the segment is not aligned
@@ -460,13 +492,44 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    const uint32_t bytes = (uint32_t)(W * B * (int)sizeof(VT));
+                    const uint32_t bytes = (uint32_t)(W * B * (int)sizeof(ST));
                     mbar_arrive_expect_tx(bar_own, bytes);
                     bulk_copy_g2s(own_s, x + seg, bytes, bar_own);
                 }
                 pending |= 1u << kMaxBuf;
             }
 
+            int nf = 0;
+            VT diag = (VT)0;
+            if constexpr (MODE == 1) {  // diagonal term, and the flips from the entry table
+                int diag4 = 0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int e = lane + 32 * h;
+                    if (e < a.n_bonds)
+                        diag4 += (2 * (int)hvp_digit(lab, s_bond[2 * e], a.bits) - a.two_s) *
+                                 (2 * (int)hvp_digit(lab, s_bond[2 * e + 1], a.bits) - a.two_s);
+                }
+                diag4 = __reduce_add_sync(kFullMask, diag4);
+                diag = a.J * (VT)diag4 * (VT)0.25;
+                const uint64_t e0 = __ldg(P.eoff + rep);
+                nf = (int)(__ldg(P.eoff + rep + 1) - e0);
+                if (a.flips && lane == 0) atomicAdd(a.flips, (unsigned long long)nf);
+                for (int base = lane; base < nf; base += 32) {
+                    const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(P.ent + e0 + base));
+                    const uint32_t tgt = raw.x, g8 = raw.y & 255u, es = (raw.y >> 8) & 255u, sidf = raw.y >> 16;
+                    VT c = halfJ;
+                    if (a.two_s != 1) {
+                        const int e = (int)(es & 127u);
+                        const int ai = (int)hvp_digit(lab, s_bond[2 * e], a.bits);
+                        const int aj = (int)hvp_digit(lab, s_bond[2 * e + 1], a.bits);
+                        c = halfJ * ((es & 128u) == 0 ? a.up[ai] * a.dn[aj] : a.dn[ai] * a.up[aj]);
+                    }
+                    f_off[base] = tgt * (uint32_t)W;
+                    f_sg[base] = (sidf << 8) | g8;
+                    f_c[base] = c * __ldg(sqrtS + sidf);
+                }
+            } else {
             // 1. images of r under the lane's elements
             LT I[GPL];
 #pragma unroll
@@ -502,9 +565,11 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                 }
             }
             diag4 = __reduce_add_sync(kFullMask, diag4);
-            const VT diag = a.J * (VT)diag4 * (VT)0.25;
-            const int nf = __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]);
+            diag = a.J * (VT)diag4 * (VT)0.25;
+            nf = __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]);
             if (a.flips && lane == 0) atomicAdd(a.flips, (unsigned long long)nf);
+            if (MODE == 2 && lane == 0 && (uint64_t)nf != P.eoff[rep + 1] - P.eoff[rep])
+                atomicOr(a.err, kErrMissingRep);  // the count pass and the kernel disagree
 
             // 3-4. search and lookup, 32 flips per round; records to shared memory
             for (int base = 0; base < nf; base += 32) {
@@ -570,7 +635,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                 if (lane < nround) {
                     const uint64_t key = (uint64_t)my_rp;
                     const uint64_t bk = key >> P.bucket_shift;
-                    uint32_t off_f = 0, sid_f = 0;
+                    uint32_t off_f = 0, sid_f = 0, idx_f = 0;
                     bool found = false;
                     if (bk < P.n_buckets) {
                         uint32_t lo = __ldg(P.bucket + bk), hi = __ldg(P.bucket + bk + 1);
@@ -591,17 +656,32 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                             found = true;
                             off_f = hrec.z;
                             sid_f = hrec.w;
+                            idx_f = lo;
                         }
                     }
                     if (!found) {
                         atomicOr(a.err, kErrMissingRep);
                         my_c = (VT)0;
                     }
-                    f_off[base + lane] = off_f;
-                    f_sg[base + lane] = (sid_f << 8) | (uint32_t)my_g;  // my_g < |G| <= 128
-                    f_c[base + lane] = my_c * __ldg(sqrtS + sid_f);      // c_a sqrt|Stab r'|
+                    if constexpr (MODE == 2) {
+                        const uint64_t slot = P.eoff[rep] + (uint64_t)(base + lane);
+                        if (slot < P.eoff[rep + 1]) {
+                            HvEntry en;
+                            en.tgt = idx_f;
+                            en.g = (uint8_t)my_g;
+                            en.esign = (uint8_t)(my_e | (my_sg < 0 ? 128 : 0));
+                            en.sid = (uint16_t)sid_f;
+                            P.ent[slot] = en;
+                        }
+                    } else {
+                        f_off[base + lane] = off_f;
+                        f_sg[base + lane] = (sid_f << 8) | (uint32_t)my_g;  // my_g < |G| <= 128
+                        f_c[base + lane] = my_c * __ldg(sqrtS + sid_f);      // c_a sqrt|Stab r'|
+                    }
                 }
             }
+            }  // search and lookup
+            if constexpr (MODE == 2) continue;  // build mode: the flips are in the table
             __syncwarp();
 
             // 5-6. gathers and contraction, Q flips per group
@@ -614,8 +694,8 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                 const int buf = grp % nbuf;
                 const int j = grp * Q + (a.tma ? lane : fg);
                 if (a.tma) {
-                    const uint32_t bytes = (lane < Q && j < nf) ? (uint32_t)(W * B * (int)sizeof(VT)) : 0u;
-                    const uint32_t total = (uint32_t)min(Q, nf - grp * Q) * (uint32_t)(W * B * (int)sizeof(VT));
+                    const uint32_t bytes = (lane < Q && j < nf) ? (uint32_t)(W * B * (int)sizeof(ST)) : 0u;
+                    const uint32_t total = (uint32_t)min(Q, nf - grp * Q) * (uint32_t)(W * B * (int)sizeof(ST));
                     const uint32_t bar = bar0 + 8 * buf;
                     fence_proxy_async_smem();  // earlier generic reads of the buffer before the async writes
                     __syncwarp();
@@ -623,14 +703,14 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                     __syncwarp();
                     if (bytes)
                         bulk_copy_g2s(stage_s + (uint32_t)(((size_t)buf * a.stage_elems + (size_t)lane * a.slot_elems) *
-                                                           sizeof(VT)),
+                                                           sizeof(ST)),
                                       x + (size_t)f_off[j] * B, bytes, bar);
                     pending |= 1u << buf;
                 } else {
                     if (j < nf && b < B) {
-                        const VT *src = x + (size_t)f_off[j] * B + b;
-                        VT *dst = stage + (size_t)buf * a.stage_elems + (size_t)fg * a.slot_elems + b;
-                        VT v[W];
+                        const ST *src = x + (size_t)f_off[j] * B + b;
+                        ST *dst = stage + (size_t)buf * a.stage_elems + (size_t)fg * a.slot_elems + b;
+                        ST v[W];
 #pragma unroll
                         for (int r = 0; r < W; ++r) v[r] = __ldg(src + r * B);
 #pragma unroll
@@ -655,7 +735,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                 if (j < nf && b < B) {
                     const int g_j = (int)(f_sg[j] & 255u);
                     const VT cf = f_c[j];
-                    const VT *xs = stage + (size_t)buf * a.stage_elems + (size_t)fg * a.slot_elems + b;
+                    const ST *xs = stage + (size_t)buf * a.stage_elems + (size_t)fg * a.slot_elems + b;
                     static_for<K>([&](auto kc) {
                         constexpr int k = decltype(kc)::value;
                         constexpr int D = SH::template D<k>;
@@ -665,7 +745,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                         const VT *R = rho_base + a.rho_off[k] + (size_t)g_j * D * RP;
                         VT u[D];
 #pragma unroll
-                        for (int g2 = 0; g2 < D; ++g2) u[g2] = xs[(Zk + g2) * B];
+                        for (int g2 = 0; g2 < D; ++g2) u[g2] = st_get<VT, ST>(xs[(Zk + g2) * B]);
                         hvp_rows<VT, D, RP>(R, u, cf, z + Zk);
                     });
                 }
@@ -695,7 +775,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                 parity ^= 1u << kMaxBuf;
                 pending &= ~(1u << kMaxBuf);
             }
-            VT *zs = stage;  // the staging buffers are idle here
+            VT *zs = reinterpret_cast<VT *>(stage);  // the staging buffers are idle here
             if (fg == 0) {
 #pragma unroll
                 for (int i = 0; i < W; ++i) zs[i * BT + b] = z[i];
@@ -719,10 +799,10 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                             val *= inv_sq;
                         }
                         const size_t e = seg + (size_t)(Zk + gam) * B + b;
-                        const VT xv = own_on ? own[(Zk + gam) * B + b] : __ldg(x + e);
-                        const VT yv = val + diag * xv;
-                        y[e] = yv;
-                        if (want_dot) dacc[k].add(xv, yv);
+                        const VT xv = st_get<VT, ST>(own_on ? own[(Zk + gam) * B + b] : __ldg(x + e));
+                        const ST ys = st_put<VT, ST>(val + diag * xv);
+                        y[e] = ys;
+                        if (want_dot) dacc[k].add(xv, st_get<VT, ST>(ys));  // the values as stored
                     }
                 });
             }
@@ -738,38 +818,48 @@ struct HvpGeom {
     int warps, nbuf, tma, tile_reps, grid, rho_smem, own;
 };
 
-template <typename VT, class SH, int GPL, bool HALF>
+template <typename VT, typename ST, class SH, int GPL, bool HALF, int MODE>
 size_t hvp_smem_t(const HvpArgs<VT> &a, int warps, int nbuf) {
     return hvp_layout<VT, HALF>(a.n_chunks, a.n_bonds, a.rho_smem ? a.rho_total : 0, warps, SH::K, SH::W, a.B, nbuf,
-                                a.stage_elems, a.tma && a.own)
+                                a.stage_elems, MODE != 2 && a.tma && a.own, (int)sizeof(ST), MODE != 1)
         .total;
 }
 
 // CTAs per SM for the given geometry (0 if it does not fit); sets the shared-memory attribute.
-template <typename VT, class SH, int GPL, bool HALF>
+template <typename VT, typename ST, class SH, int GPL, bool HALF, int MODE>
 int hvp_occupancy_t(const HvpArgs<VT> &a, int warps, int nbuf) {
-    auto kern = hvp_kernel<VT, SH, GPL, HALF>;
+    auto kern = hvp_kernel<VT, ST, SH, GPL, HALF, MODE>;
     if (warps * 32 > hvp_max_threads<VT, SH>()) return 0;
-    const size_t smem = hvp_smem_t<VT, SH, GPL, HALF>(a, warps, nbuf);
+    const size_t smem = hvp_smem_t<VT, ST, SH, GPL, HALF, MODE>(a, warps, nbuf);
     int dev = 0, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (smem > (size_t)max_smem) return 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    {  // the attribute is only ever raised: a plan made on another thread never invalidates a launch
+        static std::mutex mu;
+        static int raised[64] = {};
+        std::lock_guard<std::mutex> lk(mu);
+        const int d = dev & 63;
+        if ((int)smem > raised[d]) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                return 0;
+            raised[d] = (int)smem;
+        }
+    }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem) != cudaSuccess) return 0;
     return per_sm;
 }
 
-template <typename VT, class SH, int GPL, bool HALF>
+template <typename VT, typename ST, class SH, int GPL, bool HALF, int MODE>
 ftlm_status hvp_launch_t(HvpArgs<VT> a, const HvpGeom &geo, cudaStream_t stream) {
-    auto kern = hvp_kernel<VT, SH, GPL, HALF>;
+    auto kern = hvp_kernel<VT, ST, SH, GPL, HALF, MODE>;
     a.nbuf = geo.nbuf;
     a.tma = geo.tma;
     a.tile_reps = geo.tile_reps;
     a.rho_smem = geo.rho_smem;
     a.own = geo.own;
-    const size_t smem = hvp_smem_t<VT, SH, GPL, HALF>(a, geo.warps, geo.nbuf);
+    const size_t smem = hvp_smem_t<VT, ST, SH, GPL, HALF, MODE>(a, geo.warps, geo.nbuf);
     kern<<<(unsigned)geo.grid, geo.warps * 32, smem, stream>>>(a);
     count_launch();
     FTLM_CUDA(cudaGetLastError());

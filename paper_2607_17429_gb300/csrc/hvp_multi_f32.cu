@@ -4,9 +4,9 @@
 namespace ftlm {
 
 const HvpOps<float> *hvp_ops_multi_f32(int shape, int gpl, bool half) {
-    static const HvpOps<float> ih[2] = {FTLM_HVP_OPS(float, ShapeIh, 4, false), FTLM_HVP_OPS(float, ShapeIh, 4, true)};
-    static const HvpOps<float> oh[2] = {FTLM_HVP_OPS(float, ShapeOh, 2, false), FTLM_HVP_OPS(float, ShapeOh, 2, true)};
-    static const HvpOps<float> td[2] = {FTLM_HVP_OPS(float, ShapeTd, 2, false), FTLM_HVP_OPS(float, ShapeTd, 2, true)};
+    static const HvpOps<float> ih[2] = {FTLM_HVP_OPS(float, float, ShapeIh, 4, false), FTLM_HVP_OPS(float, float, ShapeIh, 4, true)};
+    static const HvpOps<float> oh[2] = {FTLM_HVP_OPS(float, float, ShapeOh, 2, false), FTLM_HVP_OPS(float, float, ShapeOh, 2, true)};
+    static const HvpOps<float> td[2] = {FTLM_HVP_OPS(float, float, ShapeTd, 2, false), FTLM_HVP_OPS(float, float, ShapeTd, 2, true)};
     const int h = half ? 1 : 0;
     if (shape == kShapeIh && gpl == 4) return &ih[h];
     if (shape == kShapeOh && gpl == 2) return &oh[h];

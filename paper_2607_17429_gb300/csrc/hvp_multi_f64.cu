@@ -4,9 +4,9 @@
 namespace ftlm {
 
 const HvpOps<double> *hvp_ops_multi_f64(int shape, int gpl, bool half) {
-    static const HvpOps<double> ih[2] = {FTLM_HVP_OPS(double, ShapeIh, 4, false), FTLM_HVP_OPS(double, ShapeIh, 4, true)};
-    static const HvpOps<double> oh[2] = {FTLM_HVP_OPS(double, ShapeOh, 2, false), FTLM_HVP_OPS(double, ShapeOh, 2, true)};
-    static const HvpOps<double> td[2] = {FTLM_HVP_OPS(double, ShapeTd, 2, false), FTLM_HVP_OPS(double, ShapeTd, 2, true)};
+    static const HvpOps<double> ih[2] = {FTLM_HVP_OPS(double, double, ShapeIh, 4, false), FTLM_HVP_OPS(double, double, ShapeIh, 4, true)};
+    static const HvpOps<double> oh[2] = {FTLM_HVP_OPS(double, double, ShapeOh, 2, false), FTLM_HVP_OPS(double, double, ShapeOh, 2, true)};
+    static const HvpOps<double> td[2] = {FTLM_HVP_OPS(double, double, ShapeTd, 2, false), FTLM_HVP_OPS(double, double, ShapeTd, 2, true)};
     const int h = half ? 1 : 0;
     if (shape == kShapeIh && gpl == 4) return &ih[h];
     if (shape == kShapeOh && gpl == 2) return &oh[h];

@@ -21,32 +21,56 @@ struct HvpOps {
     int max_threads;
 };
 
-#define FTLM_HVP_OPS(VT, SH, GPL, HALF) \
-    HvpOps<VT> { &hvp_occupancy_t<VT, SH, GPL, HALF>, &hvp_launch_t<VT, SH, GPL, HALF>, hvp_max_threads<VT, SH>() }
+#define FTLM_HVP_OPS_M(VT, ST, SH, GPL, HALF, MODE)                                              \
+    HvpOps<VT> {                                                                                   \
+        &hvp_occupancy_t<VT, ST, SH, GPL, HALF, MODE>, &hvp_launch_t<VT, ST, SH, GPL, HALF, MODE>, \
+            hvp_max_threads<VT, SH>()                                                              \
+    }
+#define FTLM_HVP_OPS(VT, ST, SH, GPL, HALF) FTLM_HVP_OPS_M(VT, ST, SH, GPL, HALF, 0)
 
 template <typename VT>
 struct HvpPlan {
     HvpArgs<VT> a;
     HvpGeom geo;
     const HvpOps<VT> *ops = nullptr;
+    int mode = 0;                     // 0: on-the-fly search; 1: entry table
     uint64_t rows_total = 0;          // packed rows over all parts (profiling)
     std::vector<uint64_t> tile0, ntile;  // per part: first tile and tile count
 };
 
 // packed.cu
 template <typename VT>
-void hvp_part_of(const ftlm_sector *s, const PackedSet *ps, const ftlm_basis *const *blocks, const VT *x, VT *y,
+void hvp_part_of(const ftlm_sector *s, const PackedSet *ps, const ftlm_basis *const *blocks, const void *x, void *y,
                  HvpPart<VT> &p);
+// esize: bytes of a stored vector element (sizeof(VT), or 2 for FP16 storage with VT = float)
 template <typename VT>
-ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpPart<VT>> &parts, int B,
+ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpPart<VT>> &parts, int B, int esize,
                      HvpPlan<VT> &plan, cudaStream_t tune_stream);
 template <typename VT>
 ftlm_status hvp_launch_plan(const HvpPlan<VT> &plan, double *dot_part, cudaStream_t stream, bool timed);
+// pieces of a plan (packed.cu): sector-wide arguments, geometry, tile order
+template <typename VT>
+void hvp_fill_common(const ftlm_sector *s, const PackedSet *ps, int B, int esize, HvpArgs<VT> &a);
+template <typename VT>
+ftlm_status hvp_choose_geom(const HvpOps<VT> *ops, HvpArgs<VT> a, bool tma, HvpGeom &geo);
+template <typename VT>
+void hvp_retile(HvpPlan<VT> &plan, std::vector<HvpPart<VT>> &parts);
+// entries.cu: the sector's optional entry table
+ftlm_status entry_table_build(ftlm_sector *s, cudaStream_t stream);
+void entry_table_free(ftlm_sector *s);
 
 // null if the combination is not compiled (gpl: 2 for |G| <= 64, 4 for |G| <= 128)
 const HvpOps<float> *hvp_ops_single_f32(int shape, int gpl, bool half);
 const HvpOps<float> *hvp_ops_multi_f32(int shape, int gpl, bool half);
 const HvpOps<double> *hvp_ops_single_f64(int shape, int gpl, bool half);
 const HvpOps<double> *hvp_ops_multi_f64(int shape, int gpl, bool half);
+const HvpOps<float> *hvp_ops_single_f16(int shape, int gpl, bool half);  // FP16 storage, FP32 arithmetic
+const HvpOps<float> *hvp_ops_multi_f16(int shape, int gpl, bool half);
+// table mode (flips from the sector's entry table), any shape; esize 8, 4 or 2
+const HvpOps<double> *hvp_ops_table_f64(int shape);
+const HvpOps<float> *hvp_ops_table_f32(int shape);
+const HvpOps<float> *hvp_ops_table_f16(int shape);
+// build mode (writes the entry table; no gathers or outputs)
+const HvpOps<float> *hvp_ops_build(int gpl, bool half);
 
 }  // namespace ftlm

@@ -6,8 +6,8 @@ namespace ftlm {
 const HvpOps<float> *hvp_ops_single_f32(int shape, int gpl, bool half) {
     static const HvpOps<float> tab[5][2][2] = {
 #define ROW(D) \
-    {{FTLM_HVP_OPS(float, Shape<D>, 2, false), FTLM_HVP_OPS(float, Shape<D>, 2, true)}, \
-     {FTLM_HVP_OPS(float, Shape<D>, 4, false), FTLM_HVP_OPS(float, Shape<D>, 4, true)}}
+    {{FTLM_HVP_OPS(float, float, Shape<D>, 2, false), FTLM_HVP_OPS(float, float, Shape<D>, 2, true)}, \
+     {FTLM_HVP_OPS(float, float, Shape<D>, 4, false), FTLM_HVP_OPS(float, float, Shape<D>, 4, true)}}
         ROW(1), ROW(2), ROW(3), ROW(4), ROW(5)
 #undef ROW
     };

@@ -6,8 +6,8 @@ namespace ftlm {
 const HvpOps<double> *hvp_ops_single_f64(int shape, int gpl, bool half) {
     static const HvpOps<double> tab[5][2][2] = {
 #define ROW(D) \
-    {{FTLM_HVP_OPS(double, Shape<D>, 2, false), FTLM_HVP_OPS(double, Shape<D>, 2, true)}, \
-     {FTLM_HVP_OPS(double, Shape<D>, 4, false), FTLM_HVP_OPS(double, Shape<D>, 4, true)}}
+    {{FTLM_HVP_OPS(double, double, Shape<D>, 2, false), FTLM_HVP_OPS(double, double, Shape<D>, 2, true)}, \
+     {FTLM_HVP_OPS(double, double, Shape<D>, 4, false), FTLM_HVP_OPS(double, double, Shape<D>, 4, true)}}
         ROW(1), ROW(2), ROW(3), ROW(4), ROW(5)
 #undef ROW
     };

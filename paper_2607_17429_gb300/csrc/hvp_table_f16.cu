@@ -1,0 +1,17 @@
+// Packed H·v kernels in table mode (flips read from the sector's entry table), every compiled
+// block shape, FP16 vector storage with FP32 arithmetic.
+#include "hvp_ops.h"
+
+namespace ftlm {
+
+const HvpOps<float> *hvp_ops_table_f16(int shape) {
+    static const HvpOps<float> tab[kNumShapes] = {
+        FTLM_HVP_OPS_M(float, __half, Shape<1>, 2, false, 1), FTLM_HVP_OPS_M(float, __half, Shape<2>, 2, false, 1),
+        FTLM_HVP_OPS_M(float, __half, Shape<3>, 2, false, 1), FTLM_HVP_OPS_M(float, __half, Shape<4>, 2, false, 1),
+        FTLM_HVP_OPS_M(float, __half, Shape<5>, 2, false, 1), FTLM_HVP_OPS_M(float, __half, ShapeIh, 2, false, 1),
+        FTLM_HVP_OPS_M(float, __half, ShapeOh, 2, false, 1), FTLM_HVP_OPS_M(float, __half, ShapeTd, 2, false, 1)};
+    if (shape < 0 || shape >= kNumShapes) return nullptr;
+    return &tab[shape];
+}
+
+}  // namespace ftlm

@@ -1,0 +1,17 @@
+// Packed H·v kernels in table mode (flips read from the sector's entry table), every compiled
+// block shape, double vectors.
+#include "hvp_ops.h"
+
+namespace ftlm {
+
+const HvpOps<double> *hvp_ops_table_f64(int shape) {
+    static const HvpOps<double> tab[kNumShapes] = {
+        FTLM_HVP_OPS_M(double, double, Shape<1>, 2, false, 1), FTLM_HVP_OPS_M(double, double, Shape<2>, 2, false, 1),
+        FTLM_HVP_OPS_M(double, double, Shape<3>, 2, false, 1), FTLM_HVP_OPS_M(double, double, Shape<4>, 2, false, 1),
+        FTLM_HVP_OPS_M(double, double, Shape<5>, 2, false, 1), FTLM_HVP_OPS_M(double, double, ShapeIh, 2, false, 1),
+        FTLM_HVP_OPS_M(double, double, ShapeOh, 2, false, 1), FTLM_HVP_OPS_M(double, double, ShapeTd, 2, false, 1)};
+    if (shape < 0 || shape >= kNumShapes) return nullptr;
+    return &tab[shape];
+}
+
+}  // namespace ftlm

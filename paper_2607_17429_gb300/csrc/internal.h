@@ -28,6 +28,18 @@ struct alignas(16) HvRec {
     uint32_t sid;
 };
 
+// Entry of the optional per-sector table of ladder flips (the paper's two-phase
+// design, Section 3): the flipped state's representative (index in the
+// sector), the minimising element g*, the bond and the sign of the flip
+// (bit 7: s_i^- s_j^+), and the representative's stabilizer id.  A
+// representative's entries follow the H·v kernel's flip order.
+struct alignas(8) HvEntry {
+    uint32_t tgt;
+    uint8_t g;
+    uint8_t esign;
+    uint16_t sid;
+};
+
 // Packed set: K blocks of one sector whose rows are interleaved by
 // representative, in lifted coordinates: representative r owns the W = sum_k
 // d_k rows (k, gamma), gamma < d_k, holding V_k(r) x_k(r) (Eq. 11's V_r maps a
@@ -101,6 +113,10 @@ struct ftlm_sector {
     std::vector<std::array<uint64_t, 2>> stab_masks;  // per id
     std::vector<std::vector<int>> stab_elems;         // per id
     uint32_t *d_bucket = nullptr;                     // [n_buckets + 1] first rep index of each bucket
+    uint64_t *d_eoff = nullptr;                       // entry table (optional): [n_reps + 1] first entry
+    ftlm::HvEntry *d_ent = nullptr;                   // [n_entries] per representative, in flip order
+    uint64_t n_entries = 0;
+    size_t entry_bytes = 0;
     int bucket_shift = 0;
     uint64_t n_buckets = 0;
     // H·v search tables

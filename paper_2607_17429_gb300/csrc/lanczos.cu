@@ -279,8 +279,9 @@ ftlm_status ftlm_lanczos(const ftlm_basis *b, ftlm_dtype dtype, int R, int n_ste
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const ftlm_basis *one[1] = {b};
     std::vector<LzSetIn> sets{{b->sec, b->ps, one, &block_id}};
-    if (dtype == FTLM_F64) return lanczos_packed<double>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done);
-    if (dtype == FTLM_F32) return lanczos_packed<float>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done);
+    if (dtype == FTLM_F64) return lanczos_packed<double>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done, 8);
+    if (dtype == FTLM_F32) return lanczos_packed<float>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done, 4);
+    if (dtype == FTLM_F16) return lanczos_packed<float>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done, 2);
     return fail(FTLM_EINVAL, "unknown dtype");
 }
 
@@ -307,8 +308,11 @@ ftlm_status ftlm_lanczos_multi(const ftlm_multiblock *mb, ftlm_dtype dtype, int 
     if (mb->ps) {  // packed layout: one launch per kernel for all blocks
         std::vector<LzSetIn> sets{{mb->sec, mb->ps, mb->blocks.data(), block_ids}};
         if (dtype == FTLM_F64)
-            return lanczos_packed<double>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done);
-        if (dtype == FTLM_F32) return lanczos_packed<float>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done);
+            return lanczos_packed<double>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done, 8);
+        if (dtype == FTLM_F32)
+            return lanczos_packed<float>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done, 4);
+        if (dtype == FTLM_F16)
+            return lanczos_packed<float>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done, 2);
         return fail(FTLM_EINVAL, "unknown dtype");
     }
     if (dtype == FTLM_F64)
@@ -342,8 +346,9 @@ ftlm_status ftlm_lanczos_sets(int n_sets, const ftlm_multiblock *const *sets, ft
         in.push_back({m->sec, m->ps, m->blocks.data(), block_ids + (size_t)i * K});
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    if (dtype == FTLM_F64) return lanczos_packed<double>(in, R, n_steps, seed, rng, st, alpha, beta, steps_done);
-    if (dtype == FTLM_F32) return lanczos_packed<float>(in, R, n_steps, seed, rng, st, alpha, beta, steps_done);
+    if (dtype == FTLM_F64) return lanczos_packed<double>(in, R, n_steps, seed, rng, st, alpha, beta, steps_done, 8);
+    if (dtype == FTLM_F32) return lanczos_packed<float>(in, R, n_steps, seed, rng, st, alpha, beta, steps_done, 4);
+    if (dtype == FTLM_F16) return lanczos_packed<float>(in, R, n_steps, seed, rng, st, alpha, beta, steps_done, 2);
     return fail(FTLM_EINVAL, "unknown dtype");
 }
 

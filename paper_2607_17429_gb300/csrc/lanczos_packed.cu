@@ -46,7 +46,7 @@ struct LzPart {
     const uint64_t *boff[kPMaxK];  // block k's row offsets [n_reps] (start-vector counters)
     uint32_t key1[kPMaxK];         // Philox key word 1 of block k (block id)
     int entry0;                    // index of (part, block 0, chain 0) in the state arrays: p * K * B
-    VT *y;                         // start vectors: output
+    void *y;                       // start vectors: output, of the storage type
 };
 
 template <typename VT>
@@ -66,7 +66,7 @@ struct LzArgs {
 // Start vectors u_0 (Philox per block row index and chain, lifted by V_k(r)),
 // with |u_0|^2 per (block, chain) as per-CTA partials.  Rows of representative
 // r: r W + Z_k + gamma.
-template <typename VT, int K>
+template <typename VT, typename ST, int K>
 __global__ void __launch_bounds__(kLzThreads) lzp_start(const __grid_constant__ LzArgs<VT> a) {
     __shared__ double red[kPMaxK * 32];
     const int warps = blockDim.x >> 5;
@@ -145,8 +145,10 @@ __global__ void __launch_bounds__(kLzThreads) lzp_start(const __grid_constant__ 
                             v += __ldg(Vr + q) *
                                  (VT)start_value(row0 + (uint64_t)q, a.chain0 + (uint32_t)b, a.key0, P.key1[k], a.rng);
                     }
-                    P.y[e] = v;
-                    acc[k].add(v, v);
+                    const ST sv = st_put<VT, ST>(v);
+                    static_cast<ST *>(P.y)[e] = sv;
+                    const VT vs = st_get<VT, ST>(sv);  // norms of the values as stored
+                    acc[k].add(vs, vs);
                 }
             }
         }
@@ -166,13 +168,13 @@ struct LzUpd {
     int blk_of_row[32];         // block of each row of a segment
     const uint64_t *elem0;      // [n_parts + 1] first element of each part in the vectors
     const int *entry0;          // [n_parts] p * K * B
-    VT *y;                      // in: H u_j, out: w
-    const VT *u, *up;
+    void *y;                    // in: H u_j, out: w (storage type)
+    const void *u, *up;
     const VT *coef;             // [entries][3]
     double *norm_part;          // [n_parts][gridDim.x][K][B]
 };
 
-template <typename VT>
+template <typename VT, typename ST>
 __global__ void __launch_bounds__(kLzThreads) lzp_update(const __grid_constant__ LzUpd<VT> a) {
     __shared__ double red[kLzThreads];
     const int B = a.B, WB = a.W * a.B, K = a.K;
@@ -184,9 +186,9 @@ __global__ void __launch_bounds__(kLzThreads) lzp_update(const __grid_constant__
         const uint64_t e0 = a.elem0[p], n = a.elem0[p + 1] - e0;
         const VT *c = a.coef + ((size_t)a.entry0[p] + k * B + b) * 3;
         const VT cy = c[0], cu = c[1], cp = a.has_prev ? c[2] : (VT)0;
-        VT *y = a.y + e0;
-        const VT *u = a.u + e0;
-        const VT *up = a.up + e0;
+        ST *y = static_cast<ST *>(a.y) + e0;
+        const ST *u = static_cast<const ST *>(a.u) + e0;
+        const ST *up = static_cast<const ST *>(a.up) + e0;
         DotAcc<VT> acc;
         acc.zero();
         uint64_t e = g;
@@ -194,20 +196,24 @@ __global__ void __launch_bounds__(kLzThreads) lzp_update(const __grid_constant__
             VT yv[4], uv[4], pv[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                yv[q] = y[e + q * T];
-                uv[q] = __ldg(u + e + q * T);
-                pv[q] = a.has_prev ? __ldg(up + e + q * T) : (VT)0;
+                yv[q] = st_get<VT, ST>(y[e + q * T]);
+                uv[q] = st_get<VT, ST>(__ldg(u + e + q * T));
+                pv[q] = a.has_prev ? st_get<VT, ST>(__ldg(up + e + q * T)) : (VT)0;
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const VT w = cy * yv[q] - cu * uv[q] - cp * pv[q];
-                y[e + q * T] = w;
+                const ST ws = st_put<VT, ST>(cy * yv[q] - cu * uv[q] - cp * pv[q]);
+                y[e + q * T] = ws;
+                const VT w = st_get<VT, ST>(ws);
                 acc.add(w, w);
             }
         }
         for (; e < n; e += T) {
-            const VT w = cy * y[e] - cu * __ldg(u + e) - (a.has_prev ? cp * __ldg(up + e) : (VT)0);
-            y[e] = w;
+            const VT wv = cy * st_get<VT, ST>(y[e]) - cu * st_get<VT, ST>(__ldg(u + e)) -
+                          (a.has_prev ? cp * st_get<VT, ST>(__ldg(up + e)) : (VT)0);
+            const ST ws = st_put<VT, ST>(wv);
+            y[e] = ws;
+            const VT w = st_get<VT, ST>(ws);
             acc.add(w, w);
         }
         red[threadIdx.x] = acc.value();
@@ -229,6 +235,8 @@ __global__ void __launch_bounds__(kLzThreads) lzp_update(const __grid_constant__
 struct LzState {
     double *alpha, *beta;       // [n_steps][entries]
     double *s, *s_prev, *bprev; // [entries]
+    double *sig;                // [entries] power-of-two scale of the stored u_{j+1} (FP16 storage; else 1)
+    const double *rms_rows;     // [n_parts * K] sqrt(packed rows of the block) / (16 Hmax): the scale target
     int *active, *steps;        // [entries]
     const int *m_max;           // [n_parts * K]
     double *coef64;             // [entries][3]
@@ -238,8 +246,17 @@ struct LzState {
 // One CTA per part, one thread per (block, chain).  Sums the per-CTA partials of
 // the CTAs that processed tiles of the part (tile order fixed, so the sum is too).
 // mode 0: start-vector norms; 1: alpha_j and the update coefficients; 2: beta_{j+1}.
+// With `scaled` (FP16 storage) the update writes sigma w instead of w, sigma the
+// per-block power of two 2^floor(log2(sqrt(rows) / (16 Hmax))) with Hmax = |J|
+// n_bonds s(s+1) >= |H|: since |w| = beta_{j+1} <= |H v_j| <= Hmax, the stored
+// components have a root mean square at most 1/16 and no component can exceed
+// sqrt(rows) / 16, independently of the block dimension (the subnormal range of
+// FP16 that a fixed scale would reach in large blocks is avoided).  sigma
+// multiplies the three coefficients, beta_{j+1} = |sigma w| / sigma, and the next
+// scale s_{j+1} = 1 / |sigma w| (v_{j+1} = sigma w / (sigma beta_{j+1})).  Without
+// it sigma = 1 and the recurrence is unchanged.
 __global__ void lzp_finalize(int mode, int j, int K, int B, int grid, const uint64_t *tile0, const uint64_t *ntile,
-                             const double *part, LzState st, double tol) {
+                             const double *part, LzState st, double tol, int scaled) {
     const int p = blockIdx.x, t = threadIdx.x;
     if (t >= K * B) return;
     const int k = t / B, b = t % B;
@@ -261,6 +278,7 @@ __global__ void lzp_finalize(int mode, int j, int K, int B, int grid, const uint
         st.s[e] = on ? 1.0 / n : 0.0;
         st.s_prev[e] = 0.0;
         st.bprev[e] = 0.0;
+        st.sig[e] = 1.0;
         st.active[e] = on ? 1 : 0;
         st.steps[e] = 0;
     } else if (mode == 1) {
@@ -271,6 +289,15 @@ __global__ void lzp_finalize(int mode, int j, int K, int B, int grid, const uint
             c0 = s;
             c1 = al * s;
             c2 = j > 0 ? st.bprev[e] * st.s_prev[e] : 0.0;
+            double sig = 1.0;
+            if (scaled) {
+                const double ex = floor(log2(st.rms_rows[p * K + k]));
+                sig = ldexp(1.0, (int)fmin(fmax(ex, -100.0), 100.0));
+            }
+            st.sig[e] = sig;
+            c0 *= sig;
+            c1 *= sig;
+            c2 *= sig;
         }
         st.alpha[(size_t)j * E + e] = al;
         st.coef64[3 * e] = c0;
@@ -284,38 +311,41 @@ __global__ void lzp_finalize(int mode, int j, int K, int B, int grid, const uint
             st.beta[(size_t)j * E + e] = 0.0;
             return;
         }
-        const double bn = sqrt(sum);
+        const double bn = sqrt(sum);           // |sigma w| of the stored vector
+        const double be = bn / st.sig[e];      // beta_{j+1} = |w|
         const double al = st.alpha[(size_t)j * E + e];
-        st.beta[(size_t)j * E + e] = bn;
-        if (j + 1 >= st.m_max[p * K + k] || bn <= tol * (fabs(al) + st.bprev[e])) {
+        st.beta[(size_t)j * E + e] = be;
+        if (j + 1 >= st.m_max[p * K + k] || be <= tol * (fabs(al) + st.bprev[e])) {
             st.active[e] = 0;
             st.steps[e] = j + 1;
         } else {
             st.s_prev[e] = st.s[e];
             st.s[e] = 1.0 / bn;
-            st.bprev[e] = bn;
+            st.bprev[e] = be;
         }
     }
 }
 
-template <typename VT>
+template <typename VT, typename ST>
 ftlm_status lzp_start_launch(int K, const LzArgs<VT> &a, int grid, cudaStream_t st) {
     count_launch();
     switch (K) {
-        case 1: lzp_start<VT, 1><<<grid, kLzThreads, 0, st>>>(a); break;
-        case 5: lzp_start<VT, 5><<<grid, kLzThreads, 0, st>>>(a); break;
-        case 10: lzp_start<VT, 10><<<grid, kLzThreads, 0, st>>>(a); break;
+        case 1: lzp_start<VT, ST, 1><<<grid, kLzThreads, 0, st>>>(a); break;
+        case 5: lzp_start<VT, ST, 5><<<grid, kLzThreads, 0, st>>>(a); break;
+        case 10: lzp_start<VT, ST, 10><<<grid, kLzThreads, 0, st>>>(a); break;
         default: return fail(FTLM_EUNSUPPORTED, "no recurrence kernel for %d blocks", K);
     }
     FTLM_CUDA(cudaGetLastError());
     return FTLM_OK;
 }
 
+
 }  // namespace
 
-template <typename VT>
-ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps, uint64_t seed, int rng,
-                           cudaStream_t stream, double *alpha, double *beta, int *steps_done) {
+template <typename VT, typename ST>
+ftlm_status lanczos_packed_st(const std::vector<LzSetIn> &sets, int R, int n_steps, uint64_t seed, int rng,
+                              cudaStream_t stream, double *alpha, double *beta, int *steps_done) {
+    constexpr bool kScaled = sizeof(ST) < sizeof(VT);
     const int P = (int)sets.size();
     const PackedSet *ps0 = sets[0].ps;
     const int K = ps0->K;
@@ -336,13 +366,13 @@ ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps,
     }
     if (m_all == 0) return FTLM_OK;
     const uint64_t rows = row0[P];
-    DevBuf<VT> vb[3];
+    DevBuf<ST> vb[3];
     for (int q = 0; q < 3; ++q) FTLM_CUDA(vb[q].alloc(std::max<uint64_t>(rows, 1) * Bmax));
     const size_t E = (size_t)P * K * Bmax;
     DevBuf<double> dstate;
     DevBuf<float> fstate;
     DevBuf<int> istate;
-    FTLM_CUDA(dstate.alloc(2 * (size_t)n_steps * E + 6 * E));
+    FTLM_CUDA(dstate.alloc(2 * (size_t)n_steps * E + 7 * E + (size_t)P * K));
     FTLM_CUDA(fstate.alloc(3 * E));
     FTLM_CUDA(istate.alloc(2 * E + (size_t)P * K));
     LzState st;
@@ -352,16 +382,32 @@ ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps,
     st.s_prev = st.s + E;
     st.bprev = st.s_prev + E;
     st.coef64 = st.bprev + E;
+    st.sig = st.coef64 + 3 * E;
+    st.rms_rows = st.sig + E;
+    {
+        std::vector<double> rr((size_t)P * K);
+        for (int p = 0; p < P; ++p) {
+            const ftlm_sector *sp = sets[p].sec;
+            const double sp1 = 0.5 * sp->two_s * (0.5 * sp->two_s + 1.0);
+            const double hmax = std::max(1e-300, fabs(sp->grp.J) * sp->grp.n_bonds() * sp1);  // >= |H|
+            for (int k = 0; k < K; ++k)
+                rr[(size_t)p * K + k] = sqrt((double)sp->n_reps * ps0->dims[k]) / (16.0 * hmax);
+        }
+        FTLM_CUDA(cudaMemcpyAsync(st.sig + E, rr.data(), rr.size() * 8, cudaMemcpyHostToDevice, stream));
+    }
     st.coef32 = fstate.p;
     st.active = istate.p;
     st.steps = istate.p + E;
     st.m_max = istate.p + 2 * E;
     FTLM_CUDA(cudaMemcpyAsync(istate.p + 2 * E, m_max.data(), m_max.size() * sizeof(int), cudaMemcpyHostToDevice,
                               stream));
+    DevBuf<int> derr;
+    FTLM_CUDA(derr.alloc(1));
+    FTLM_CUDA(cudaMemsetAsync(derr.p, 0, sizeof(int), stream));
     int dev = 0, sms = kNumSMs;
     FTLM_CUDA(cudaGetDevice(&dev));
     FTLM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const double tol = sizeof(VT) == 8 ? 1e-12 : 1e-6;
+    const double tol = sizeof(ST) == 8 ? 1e-12 : (sizeof(ST) == 4 ? 1e-6 : 1e-3);
     const char *ng = getenv("FTLM_NO_GRAPH");
     const bool use_graph = !(ng && strcmp(ng, "1") == 0);
     std::vector<double> ha, hb;
@@ -379,8 +425,9 @@ ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps,
             for (int p = 0; p < P; ++p)
                 hvp_part_of<VT>(sets[p].sec, sets[p].ps, sets[p].blocks, vb[q].p + row0[p] * B,
                                 vb[(q + 1) % 3].p + row0[p] * B, hparts[q][p]);
-            ftlm_status s0 = hvp_plan<VT>(sets[0].sec, ps0, hparts[q], B, plan[q], stream);
+            ftlm_status s0 = hvp_plan<VT>(sets[0].sec, ps0, hparts[q], B, (int)sizeof(ST), plan[q], stream);
             if (s0 != FTLM_OK) return s0;
+            plan[q].a.err = derr.p;  // this call's own error word (launches on the same sector may run concurrently)
             plan[q].rows_total = rows;
             if (P > 1) {
                 FTLM_CUDA(d_hparts[q].alloc(P));
@@ -505,10 +552,10 @@ ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps,
             U.norm_part = up_part.p;
         }
         // ---- start vectors and their norms
-        ftlm_status s1 = lzp_start_launch<VT>(K, la, lz_grid, stream);
+        ftlm_status s1 = lzp_start_launch<VT, ST>(K, la, lz_grid, stream);
         if (s1 != FTLM_OK) return s1;
         count_launch();
-        lzp_finalize<<<P, K * B, 0, stream>>>(0, 0, K, B, lz_grid, lz_t0, lz_nt, lz_part.p, st, tol);
+        lzp_finalize<<<P, K * B, 0, stream>>>(0, 0, K, B, lz_grid, lz_t0, lz_nt, lz_part.p, st, tol, kScaled);
         FTLM_CUDA(cudaGetLastError());
         // ---- the step loop (captured once on a private stream, replayed once on the caller's)
         const bool prof = profiling_on();
@@ -531,15 +578,16 @@ ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps,
                     FTLM_CUDA(capture ? cudaEventRecordWithFlags(ev.back(), ss, cudaEventRecordExternal)
                                       : cudaEventRecord(ev.back(), ss));
                 count_launch();
-                lzp_finalize<<<P, K * B, 0, ss>>>(1, j, K, B, hv_grid, hv_t0, hv_nt, hv_part.p, st, tol);
+                lzp_finalize<<<P, K * B, 0, ss>>>(1, j, K, B, hv_grid, hv_t0, hv_nt, hv_part.p, st, tol, kScaled);
                 FTLM_CUDA(cudaGetLastError());
                 LzUpd<VT> U = ua[q];
                 U.has_prev = j > 0;
                 count_launch();
-                lzp_update<VT><<<up_grid, kLzThreads, 0, ss>>>(U);
+                lzp_update<VT, ST><<<up_grid, kLzThreads, 0, ss>>>(U);
                 FTLM_CUDA(cudaGetLastError());
                 count_launch();
-                lzp_finalize<<<P, K * B, 0, ss>>>(2, j, K, B, up_grid, d_ut.p, d_ut.p + P, up_part.p, st, tol);
+                lzp_finalize<<<P, K * B, 0, ss>>>(2, j, K, B, up_grid, d_ut.p, d_ut.p + P, up_part.p, st, tol,
+                                                  kScaled);
                 FTLM_CUDA(cudaGetLastError());
             }
             return FTLM_OK;
@@ -591,11 +639,11 @@ ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps,
         FTLM_CUDA(cudaMemcpyAsync(hb.data(), st.beta, (size_t)n_steps * E * 8, cudaMemcpyDeviceToHost, stream));
         FTLM_CUDA(cudaMemcpyAsync(hs.data(), st.steps, E * sizeof(int), cudaMemcpyDeviceToHost, stream));
         FTLM_CUDA(cudaStreamSynchronize(stream));
-        for (int p = 0; p < P; ++p) {
+        {
             int err = 0;
-            FTLM_CUDA(cudaMemcpy(&err, sets[p].sec->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+            FTLM_CUDA(cudaMemcpyAsync(&err, derr.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
+            FTLM_CUDA(cudaStreamSynchronize(stream));
             if (err) {
-                cudaMemset(sets[p].sec->d_err, 0, sizeof(int));
                 if (err & kErrWaitTimeout) return fail(FTLM_ETIMEOUT, "a bounded device wait gave up in H·v");
                 return fail(FTLM_EINTERNAL, "device bounds check tripped in H·v (code %d)", err);
             }
@@ -616,9 +664,21 @@ ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps,
     return FTLM_OK;
 }
 
+template <typename VT>
+ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps, uint64_t seed, int rng,
+                           cudaStream_t stream, double *alpha, double *beta, int *steps_done, int esize) {
+    if (esize == (int)sizeof(VT))
+        return lanczos_packed_st<VT, VT>(sets, R, n_steps, seed, rng, stream, alpha, beta, steps_done);
+    if constexpr (sizeof(VT) == 4) {
+        if (esize == 2)
+            return lanczos_packed_st<float, __half>(sets, R, n_steps, seed, rng, stream, alpha, beta, steps_done);
+    }
+    return fail(FTLM_EINVAL, "no %d-byte storage for this arithmetic type", esize);
+}
+
 template ftlm_status lanczos_packed<float>(const std::vector<LzSetIn> &, int, int, uint64_t, int, cudaStream_t,
-                                           double *, double *, int *);
+                                           double *, double *, int *, int);
 template ftlm_status lanczos_packed<double>(const std::vector<LzSetIn> &, int, int, uint64_t, int, cudaStream_t,
-                                            double *, double *, int *);
+                                            double *, double *, int *, int);
 
 }  // namespace ftlm

@@ -19,9 +19,10 @@ struct LzSetIn {
 
 // R chains on every block of every set, n_steps steps (Section 2.2).  alpha,
 // beta: host [n_sets][K][R][n_steps]; steps_done: host [n_sets][K][R].  All
-// sets share the group, spin, block shape and irreps.
+// sets share the group, spin, block shape and irreps.  esize: bytes of a stored
+// vector element, sizeof(VT) or 2 (FP16 storage, VT = float).
 template <typename VT>
 ftlm_status lanczos_packed(const std::vector<LzSetIn> &sets, int R, int n_steps, uint64_t seed, int rng,
-                           cudaStream_t stream, double *alpha, double *beta, int *steps_done);
+                           cudaStream_t stream, double *alpha, double *beta, int *steps_done, int esize);
 
 }  // namespace ftlm

@@ -220,20 +220,26 @@ ftlm_status packed_set_build(ftlm_sector *s, int K, const ftlm_basis *const *blo
 
 // ---------------------------------------------------------------- launch assembly
 
+// mode 0: on-the-fly search; 1: flips from the sector's entry table
 template <typename VT>
-const HvpOps<VT> *hvp_ops(int shape, int gpl, bool half);
+const HvpOps<VT> *hvp_ops(int shape, int gpl, bool half, int esize, int mode);
 template <>
-const HvpOps<float> *hvp_ops<float>(int shape, int gpl, bool half) {
+const HvpOps<float> *hvp_ops<float>(int shape, int gpl, bool half, int esize, int mode) {
+    if (mode == 1) return esize == 2 ? hvp_ops_table_f16(shape) : hvp_ops_table_f32(shape);
+    if (esize == 2)
+        return shape <= kShapeD5 ? hvp_ops_single_f16(shape, gpl, half) : hvp_ops_multi_f16(shape, gpl, half);
     return shape <= kShapeD5 ? hvp_ops_single_f32(shape, gpl, half) : hvp_ops_multi_f32(shape, gpl, half);
 }
 template <>
-const HvpOps<double> *hvp_ops<double>(int shape, int gpl, bool half) {
+const HvpOps<double> *hvp_ops<double>(int shape, int gpl, bool half, int esize, int mode) {
+    if (esize != 8) return nullptr;
+    if (mode == 1) return hvp_ops_table_f64(shape);
     return shape <= kShapeD5 ? hvp_ops_single_f64(shape, gpl, half) : hvp_ops_multi_f64(shape, gpl, half);
 }
 
 // Sector-wide part of the arguments (search tables, coefficients, irreps of the set).
 template <typename VT>
-void hvp_fill_common(const ftlm_sector *s, const PackedSet *ps, int B, HvpArgs<VT> &a) {
+void hvp_fill_common(const ftlm_sector *s, const PackedSet *ps, int B, int esize, HvpArgs<VT> &a) {
     memset(&a, 0, sizeof(a));
     a.N = s->N;
     a.G = s->G;
@@ -270,32 +276,33 @@ void hvp_fill_common(const ftlm_sector *s, const PackedSet *ps, int B, HvpArgs<V
     a.B = B;
     a.BT = bt;
     a.lgBT = lg;
-    const int per16 = 16 / (int)sizeof(VT);
+    a.esize = esize;
+    const int per16 = 16 / esize;
     a.slot_elems = (ps->W * B + per16 - 1) / per16 * per16;
     // Pad the slot so that the Q flip groups' slots start in different bank windows: a contraction
-    // load reads word  fg * slot_words + row * B * esize/4 + b * esize/4  in every lane (fg, b), and the
-    // Q windows of bt * esize/4 words then tile the 32 banks (slot_words an odd multiple of the window;
-    // windows below 4 words keep the 16-byte slot alignment the bulk copies need).
+    // load reads byte  fg * slot_bytes + row * B * esize + b * esize  in every lane (fg, b), and the
+    // Q windows of bt * esize bytes then tile the 32 four-byte banks (slot_bytes an odd multiple of the
+    // window; windows below 16 bytes keep the 16-byte slot alignment the bulk copies need).
     {
-        const int ew = (int)sizeof(VT) / 4;
-        const int unit = std::max(4, bt * ew);
-        if (unit < 32)
+        const int unit = std::max(16, bt * esize);
+        if (unit < 128)
             for (int i = 0; i < 16; ++i) {
-                const int sw = a.slot_elems * ew;
-                if (sw % unit == 0 && (sw / unit) % 2 == 1) break;
+                const int sb = a.slot_elems * esize;
+                if (sb % unit == 0 && (sb / unit) % 2 == 1) break;
                 a.slot_elems += per16;
             }
     }
     const int Q = 32 / bt;
     int st = Q * a.slot_elems;
-    st = std::max(st, ps->W * bt);
+    // the epilogue reuses the staging buffer for W x bt arithmetic values
+    st = std::max(st, (int)((ps->W * bt * sizeof(VT) + esize - 1) / esize));
     a.stage_elems = (st + per16 - 1) / per16 * per16;
     a.wait_limit = wait_limit_cycles();
     a.err = s->d_err;
 }
 
 template <typename VT>
-void hvp_part_of(const ftlm_sector *s, const PackedSet *ps, const ftlm_basis *const *blocks, const VT *x, VT *y,
+void hvp_part_of(const ftlm_sector *s, const PackedSet *ps, const ftlm_basis *const *blocks, const void *x, void *y,
                  HvpPart<VT> &p) {
     memset(&p, 0, sizeof(p));
     p.n_reps = s->n_reps;
@@ -314,6 +321,8 @@ void hvp_part_of(const ftlm_sector *s, const PackedSet *ps, const ftlm_basis *co
     }
     p.x = x;
     p.y = y;
+    p.eoff = s->d_eoff;
+    p.ent = s->d_ent;
 }
 
 // Geometry: the most warps (up to the kernel's bound) whose shared memory fits;
@@ -376,9 +385,10 @@ ftlm_status hvp_choose_geom(const HvpOps<VT> *ops, HvpArgs<VT> a, bool tma, HvpG
 // changes timing only.
 
 struct TuneKey {
-    int shape, gpl, half, vt, B, tma, lg;
+    int shape, gpl, half, vt, B, tma, lg, mode;
     bool operator<(const TuneKey &o) const {
-        return std::tie(shape, gpl, half, vt, B, tma, lg) < std::tie(o.shape, o.gpl, o.half, o.vt, o.B, o.tma, o.lg);
+        return std::tie(shape, gpl, half, vt, B, tma, lg, mode) <
+               std::tie(o.shape, o.gpl, o.half, o.vt, o.B, o.tma, o.lg, o.mode);
     }
 };
 struct TuneVal {
@@ -496,16 +506,19 @@ ftlm_status hvp_tune(HvpPlan<VT> &plan, std::vector<HvpPart<VT>> &parts, bool tm
 // arguments; several need a device array of descriptors (HvpPlan::a.parts),
 // filled by the caller before the launch and kept alive until it ends.
 template <typename VT>
-ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpPart<VT>> &parts, int B,
+ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpPart<VT>> &parts, int B, int esize,
                      HvpPlan<VT> &plan, cudaStream_t tune_stream) {
     if (ps->shape < 0) return fail(FTLM_EUNSUPPORTED, "no compiled packed kernel for this block set");
     HvpArgs<VT> &a = plan.a;
-    hvp_fill_common<VT>(s, ps, B, a);
+    hvp_fill_common<VT>(s, ps, B, esize, a);
     const int gpl = s->G <= 64 ? 2 : 4;
-    plan.ops = hvp_ops<VT>(ps->shape, gpl, s->half);
+    int mode = 1;  // the entry-table path when every part's sector has a table
+    for (auto &p : parts) mode = mode && p.eoff && p.ent;
+    plan.mode = mode;
+    plan.ops = hvp_ops<VT>(ps->shape, gpl, s->half, esize, mode);
     if (!plan.ops)
         return fail(FTLM_EUNSUPPORTED, "no compiled packed kernel for shape %d with |G| = %d", ps->shape, s->G);
-    bool tma = (B * (int)sizeof(VT)) % 16 == 0;
+    bool tma = (B * esize) % 16 == 0;
     uint64_t n_reps_total = 0;
     for (auto &p : parts) {
         tma = tma && ((uintptr_t)p.x % 16) == 0;
@@ -519,7 +532,7 @@ ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpP
     if (g_autotune.load() && !getenv("FTLM_HV_WARPS") && !getenv("FTLM_HV_NBUF")) {
         int lg = 0;
         while ((1ull << lg) < n_reps_total) ++lg;
-        const TuneKey key{ps->shape, gpl, s->half ? 1 : 0, (int)sizeof(VT), B, tma ? 1 : 0, lg};
+        const TuneKey key{ps->shape, gpl, s->half ? 1 : 0, esize, B, tma ? 1 : 0, lg, mode};
         std::unique_lock<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
@@ -536,9 +549,9 @@ ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpP
     hvp_retile<VT>(plan, parts);
     const uint64_t tiles = a.n_tiles;
     if (getenv("FTLM_HV_VERBOSE"))
-        fprintf(stderr, "ftlm hvp plan: shape %d B %d warps %d nbuf %d tma %d rho_smem %d own %d grid %d tiles %llu "
-                        "tile_reps %d wait_limit %llu\n",
-                ps->shape, B, plan.geo.warps, plan.geo.nbuf, plan.geo.tma, plan.geo.rho_smem, plan.geo.own,
+        fprintf(stderr, "ftlm hvp plan: shape %d B %d mode %d warps %d nbuf %d tma %d rho_smem %d own %d grid %d "
+                        "tiles %llu tile_reps %d wait_limit %llu\n",
+                ps->shape, B, mode, plan.geo.warps, plan.geo.nbuf, plan.geo.tma, plan.geo.rho_smem, plan.geo.own,
                 plan.geo.grid, (unsigned long long)tiles, plan.geo.tile_reps, (unsigned long long)a.wait_limit);
     a.parts = nullptr;
     return FTLM_OK;
@@ -609,7 +622,7 @@ ftlm_status hv_block(const ftlm_basis *b, int B, const VT *x, VT *y, cudaStream_
         std::vector<HvpPart<VT>> parts(1);
         hvp_part_of<VT>(b->sec, ps, one, xl, yl, parts[0]);
         HvpPlan<VT> plan;
-        st = hvp_plan<VT>(b->sec, ps, parts, B, plan, stream);
+        st = hvp_plan<VT>(b->sec, ps, parts, B, (int)sizeof(VT), plan, stream);
         plan.rows_total = ps->rows;
         if (st == FTLM_OK) st = hvp_launch_plan<VT>(plan, nullptr, stream, true);
     }
@@ -620,27 +633,30 @@ ftlm_status hv_block(const ftlm_basis *b, int B, const VT *x, VT *y, cudaStream_
 }
 
 template <typename VT>
-ftlm_status hvp_run_one(const ftlm_sector *s, const PackedSet *ps, const ftlm_basis *const *blocks, int B, const VT *x,
-                        VT *y, cudaStream_t stream) {
+ftlm_status hvp_run_one(const ftlm_sector *s, const PackedSet *ps, const ftlm_basis *const *blocks, int B, int esize,
+                        const void *x, void *y, cudaStream_t stream) {
     std::vector<HvpPart<VT>> parts(1);
     hvp_part_of<VT>(s, ps, blocks, x, y, parts[0]);
     HvpPlan<VT> plan;
-    ftlm_status st = hvp_plan<VT>(s, ps, parts, B, plan, stream);
+    ftlm_status st = hvp_plan<VT>(s, ps, parts, B, esize, plan, stream);
     if (st != FTLM_OK) return st;
     plan.rows_total = ps->rows;
     return hvp_launch_plan<VT>(plan, nullptr, stream, true);
 }
 
 template ftlm_status hvp_plan<float>(const ftlm_sector *, const PackedSet *, std::vector<HvpPart<float>> &, int,
-                                     HvpPlan<float> &, cudaStream_t);
+                                     int, HvpPlan<float> &, cudaStream_t);
 template ftlm_status hvp_plan<double>(const ftlm_sector *, const PackedSet *, std::vector<HvpPart<double>> &, int,
-                                      HvpPlan<double> &, cudaStream_t);
+                                      int, HvpPlan<double> &, cudaStream_t);
+template void hvp_fill_common<float>(const ftlm_sector *, const PackedSet *, int, int, HvpArgs<float> &);
+template ftlm_status hvp_choose_geom<float>(const HvpOps<float> *, HvpArgs<float>, bool, HvpGeom &);
+template void hvp_retile<float>(HvpPlan<float> &, std::vector<HvpPart<float>> &);
 template ftlm_status hvp_launch_plan<float>(const HvpPlan<float> &, double *, cudaStream_t, bool);
 template ftlm_status hvp_launch_plan<double>(const HvpPlan<double> &, double *, cudaStream_t, bool);
-template void hvp_part_of<float>(const ftlm_sector *, const PackedSet *, const ftlm_basis *const *, const float *,
-                                 float *, HvpPart<float> &);
-template void hvp_part_of<double>(const ftlm_sector *, const PackedSet *, const ftlm_basis *const *, const double *,
-                                  double *, HvpPart<double> &);
+template void hvp_part_of<float>(const ftlm_sector *, const PackedSet *, const ftlm_basis *const *, const void *,
+                                 void *, HvpPart<float> &);
+template void hvp_part_of<double>(const ftlm_sector *, const PackedSet *, const ftlm_basis *const *, const void *,
+                                  void *, HvpPart<double> &);
 
 template <typename VT>
 ftlm_status pack_impl(const ftlm_multiblock *mb, int B, VT *const *blk, VT *packed, int to_packed,
@@ -687,9 +703,9 @@ ftlm_status ftlm_hv_packed(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, c
     if (mb->ps->rows == 0) return FTLM_OK;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const ftlm_basis *const *bl = mb->blocks.data();
-    if (dtype == FTLM_F64)
-        return hvp_run_one<double>(mb->sec, mb->ps, bl, B, (const double *)x, (double *)y, st);
-    if (dtype == FTLM_F32) return hvp_run_one<float>(mb->sec, mb->ps, bl, B, (const float *)x, (float *)y, st);
+    if (dtype == FTLM_F64) return hvp_run_one<double>(mb->sec, mb->ps, bl, B, 8, x, y, st);
+    if (dtype == FTLM_F32) return hvp_run_one<float>(mb->sec, mb->ps, bl, B, 4, x, y, st);
+    if (dtype == FTLM_F16) return hvp_run_one<float>(mb->sec, mb->ps, bl, B, 2, x, y, st);
     return fail(FTLM_EINVAL, "unknown dtype");
 }
 

@@ -190,7 +190,7 @@ void fail_job(ftlm_server *S, Job *J, ftlm_status st, const std::string &msg) {
 // Bytes a job's Lanczos launch allocates: three packed vectors, the scale and
 // coefficient state, and the per-CTA dot partials.
 size_t vector_bytes(const ftlm_basis *b, const ftlm_job &j) {
-    const size_t e = j.dtype == FTLM_F64 ? 8 : 4;
+    const size_t e = j.dtype == FTLM_F64 ? 8 : (j.dtype == FTLM_F16 ? 2 : 4);
     const size_t B = (size_t)std::min(j.R, kMaxB);
     const size_t rows = b->ps ? b->ps->rows : b->dim;
     return 3 * std::max<size_t>(rows, 1) * B * e + (2 * (size_t)j.n_steps + 16) * B * 8 + 4 * kNumSMs * B * 8 +
@@ -373,9 +373,11 @@ void worker_main(ftlm_server *S) {
         }
         std::vector<double> A((size_t)P * R * nmax), Bt((size_t)P * R * nmax);
         std::vector<int> Sd((size_t)P * R);
-        ftlm_status st = js.dtype == FTLM_F64
-                             ? lanczos_packed<double>(sets, R, nmax, js.seed, js.rng, ws, A.data(), Bt.data(), Sd.data())
-                             : lanczos_packed<float>(sets, R, nmax, js.seed, js.rng, ws, A.data(), Bt.data(), Sd.data());
+        ftlm_status st =
+            js.dtype == FTLM_F64
+                ? lanczos_packed<double>(sets, R, nmax, js.seed, js.rng, ws, A.data(), Bt.data(), Sd.data(), 8)
+                : lanczos_packed<float>(sets, R, nmax, js.seed, js.rng, ws, A.data(), Bt.data(), Sd.data(),
+                                        js.dtype == FTLM_F16 ? 2 : 4);
         const std::string msg = st == FTLM_OK ? "" : ftlm_last_error();
 
         lk.lock();
@@ -451,7 +453,8 @@ ftlm_status ftlm_server_submit(ftlm_server *S, const ftlm_job *job, uint64_t *jo
     if (!job->group) return fail(FTLM_EINVAL, "job without a group");
     if (job->R < 1 || job->R > kMaxB) return fail(FTLM_EINVAL, "R must be in 1..%d", kMaxB);
     if (job->n_steps < 1 || job->n_steps > kMaxSteps) return fail(FTLM_EINVAL, "n_steps must be in 1..%d", kMaxSteps);
-    if (job->dtype != FTLM_F32 && job->dtype != FTLM_F64) return fail(FTLM_EINVAL, "unknown dtype");
+    if (job->dtype != FTLM_F32 && job->dtype != FTLM_F64 && job->dtype != FTLM_F16)
+        return fail(FTLM_EINVAL, "unknown dtype");
     if (job->rng != FTLM_GAUSS && job->rng != FTLM_RADEMACHER) return fail(FTLM_EINVAL, "unknown rng");
     const GroupData &g = job->group->d;
     if (job->irrep < 0 || job->irrep >= (int)g.irreps.size())

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 OK, EINVAL, ENOTGROUP, EBONDS, EIRREP, EUNSUPPORTED, ENOMEM, ECUDA, ETIMEOUT, EINTERNAL = range(10)
-F64, F32 = 0, 1
+F64, F32, F16 = 0, 1, 2
 GAUSS, RADEMACHER = 0, 1
 
 LIB_PATH = _build.LIB
@@ -99,6 +99,8 @@ _SIGS = {
     "ftlm_autotune_report": [_P, ctypes.c_size_t],
     "ftlm_fill_label_keyed": [_P, _I, _I, _U64, _P, _P],
     "ftlm_basis_rows": [_P, _I, _P, _P, _P, _P],
+    "ftlm_sector_build_entries": [_P, _P, _P],
+    "ftlm_sector_free_entries": [_P],
     "ftlm_server_create": [ctypes.c_size_t, _I, _I, _P],
     "ftlm_server_submit": [_P, _P, _P],
     "ftlm_server_wait": [_P, _U64, ctypes.c_double, _P, _P, _P, _P],
@@ -155,7 +157,7 @@ def _dev(a, dtype=None, numel=None, what="array"):
 
 
 def _vt(dtype):
-    return {F32: "float32", F64: "float64"}.get(dtype)
+    return {F32: "float32", F64: "float64", F16: "float16"}.get(dtype)
 
 
 def _stream(s):
@@ -289,6 +291,17 @@ def ftlm_sector_export(s: Sector):
     masks = np.zeros((n, 2), dtype=np.uint64)
     _check(_lib.ftlm_sector_export(s.handle, _ptr(labels), _ptr(masks)))
     return labels, masks
+
+
+def ftlm_sector_build_entries(s: Sector, stream=None) -> int:
+    """Build the sector's entry table (flips -> target, g*, stabilizer); returns the entry count."""
+    n = _U64()
+    _check(_lib.ftlm_sector_build_entries(s.handle, _stream(stream), ctypes.byref(n)))
+    return n.value
+
+
+def ftlm_sector_free_entries(s: Sector) -> None:
+    _check(_lib.ftlm_sector_free_entries(s.handle))
 
 
 def ftlm_build_block(s: Sector, irrep: int, stream=None) -> Basis:
