@@ -98,7 +98,10 @@ def projected_basis(block, labels):
         for gi in range(G):
             b = [0] * sec.n_sites
             for k, p in enumerate(g.perms[gi]):
-                b[p] = a[k]
+                if p < sec.n_sites:
+                    b[p] = a[k]
+                else:  # element of G x Z_2 with the spin flip: the digit moves as 2s - a_k
+                    b[p - sec.n_sites] = sec.d - 1 - a[k]
             row = pos[_label(b, sec.d)]
             coef = (g.irreps[block.irrep].rho[gi] @ V)[0, :nr]  # real irreps: rho^* = rho
             Psi[row, block.off[i]:block.off[i] + nr] += dG / (G * math.sqrt(lam)) * coef

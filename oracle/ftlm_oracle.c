@@ -4,7 +4,10 @@
  *
  * Labels use the paper's base-d encoding, Eq. 2: n = sum_k a_k d^k with
  * a_k = m_k + s and d = 2s + 1.  A group element acts by moving the digit of
- * site k to site pi_g(k) (Section 2.3), so (U(g) n)_{pi_g(k)} = n_k.
+ * site k to site pi_g(k) (Section 2.3), so (U(g) n)_{pi_g(k)} = n_k.  An entry
+ * pi_g(k) >= N marks an element of G x Z_2 that also applies the global spin
+ * flip m -> -m (Section 2.2, M = 0): the digit of site k moves to site
+ * pi_g(k) - N as 2s - a_k.
  *
  * or_enumerate: every label of the M sector (digit sum A), kept when it is the
  *   smallest label of its orbit (Section 2.3), with its stabilizer (Eq. 8).
@@ -43,14 +46,19 @@ static uint64_t encode(const int *a, int N, int d) {
     return n;
 }
 
-/* b = digits of U(g) applied to digits a: b[pi_g(k)] = a[k] */
-static void act(const int32_t *pi, const int *a, int *b, int N) {
-    for (int k = 0; k < N; ++k) b[pi[k]] = a[k];
+/* b = digits of U(g) applied to digits a: b[pi_g(k)] = a[k] (b[pi_g(k) - N] = d - 1 - a[k] when flipped) */
+static void act(const int32_t *pi, const int *a, int *b, int N, int d) {
+    for (int k = 0; k < N; ++k) {
+        if (pi[k] < N)
+            b[pi[k]] = a[k];
+        else
+            b[pi[k] - N] = d - 1 - a[k];
+    }
 }
 
 static uint64_t image(const int32_t *pi, const int *a, int N, int d) {
     int b[OR_MAXN];
-    act(pi, a, b, N);
+    act(pi, a, b, N, d);
     return encode(b, N, d);
 }
 
@@ -127,7 +135,7 @@ int64_t or_enumerate(int N, int d, int A, int G, const int32_t *perms, uint64_t 
             int is_min = 1;
             memset(mask, 0, sizeof(mask));
             for (int g = 0; g < G; ++g) {
-                act(perms + (size_t)g * N, a, b, N);
+                act(perms + (size_t)g * N, a, b, N, d);
                 uint64_t v = encode(b, N, d);
                 if (v < n) {
                     is_min = 0;

@@ -194,3 +194,32 @@ class Group:
 
     def element(self, perm):
         return self.index[tuple(int(v) for v in perm)]
+
+
+class SpinFlipExtended:
+    """G x Z_2 at M = 0 (Section 2.2): the global spin flip m -> -m commutes with H and with
+    every site permutation.  Element (g, z) has canonical index g + z |G| (z = 1 after all of
+    G) and is stored as the signed permutation pi_g(k) + z N: the digit of site k moves to
+    pi_g(k) as a_k (z = 0) or as 2s - a_k (z = 1).  Each real irrep Gamma of G gives
+    Gamma+ (rho(g, z) = rho(g)) and Gamma- (rho(g, z) = (-1)^z rho(g)); in the canonical irrep
+    order (dimension, then characters descending) they are interleaved: 2i -> Gamma_i+,
+    2i + 1 -> Gamma_i-."""
+
+    def __init__(self, group):
+        self.base = group
+        G, N = group.order, group.n_sites
+        self.order = 2 * G
+        self.n_sites = N
+        self.perms = np.concatenate([group.perms, group.perms + N]).astype(np.int32)
+        self.inv = np.concatenate([group.inv, group.inv + G])
+        self.mult = np.empty((2 * G, 2 * G), dtype=np.int64)
+        for z in (0, 1):
+            for w in (0, 1):
+                self.mult[z * G:(z + 1) * G, w * G:(w + 1) * G] = group.mult + ((z ^ w) * G)
+        self.classes = [list(c) for c in group.classes] + [[g + G for g in c] for c in group.classes]
+        self.irreps = []
+        for ir in group.irreps:
+            for sgn in (1.0, -1.0):
+                rho = None if ir.rho is None else np.concatenate([ir.rho, sgn * ir.rho])
+                self.irreps.append(Irrep(ir.dim, ir.fs, np.concatenate([ir.chars, sgn * ir.chars]), rho))
+        self.char_table = np.array([ir.chars for ir in self.irreps])

@@ -4,7 +4,8 @@
   digit sum is A_tot = N s + M (Section 2.1), by the plain counting recursion
   over sites.
 * ``fixed_count``: number of M-sector product states left unchanged by one site
-  permutation: the digits must be constant on every cycle of the permutation.
+  permutation: the digits must be constant on every cycle of the permutation
+  (with the spin flip of G x Z_2 at M = 0: alternate between a and 2s - a).
 * ``block_dim``: the single-partner-row block dimension of irrep Gamma, i.e. the
   multiplicity of Gamma in the permutation representation on the M sector,
   (1/|G|) sum_g chi_Gamma(g) * fixed_count(g)  (equals Eq. 13 summed over the
@@ -64,9 +65,24 @@ def cycle_lengths(perm) -> list[int]:
 
 
 def fixed_count(perm, two_s: int, two_M: int) -> int:
-    A = digit_total(len(perm), two_s, two_M)
-    if A < 0 or A > len(perm) * two_s:
+    N = len(perm)
+    A = digit_total(N, two_s, two_M)
+    if A < 0 or A > N * two_s:
         return 0
+    if any(p >= N for p in perm):
+        # element of G x Z_2 with the spin flip (entries pi(k) + N): a fixed state has
+        # a_{pi(k)} = 2s - a_k, so along a cycle the digits alternate a, 2s - a.  An even
+        # cycle takes any a (its digit sum is len * s); an odd one needs a = s, possible
+        # only for integer s.  Every fixed state then has digit sum N s, i.e. M = 0.
+        if two_M != 0:
+            return 0
+        count = 1
+        for ell in cycle_lengths([p % N for p in perm]):
+            if ell % 2 == 0:
+                count *= two_s + 1
+            elif two_s % 2:
+                return 0
+        return count
     return count_strings(cycle_lengths(perm), two_s, A)
 
 
