@@ -270,21 +270,23 @@ def _kernel_sha():
     return h.hexdigest()[:16]
 
 
-def _traffic_record(dtype_name, mode):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+def _traffic_record(dtype_name, mode, workload):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source and workload."""
     sha = _kernel_sha()
     path = os.path.join(ROOT, "profiles", "roofline_traffic.md")
     try:
         for ln in open(path):
             p = ln.split()
-            if len(p) >= 5 and p[0] == "hvp_kernel" and p[1] == dtype_name and p[3] == sha and p[4] == mode:
+            if (len(p) >= 6 and p[0] == "hvp_kernel" and p[1] == dtype_name and p[3] == sha and p[4] == mode
+                    and p[5] == workload):
                 return float(p[2])
     except OSError:
         pass
     return None
 
 
-def hv_roofline(prof, dtype_name, flips, n_reps, W, B, esize, mode="search"):
+def hv_roofline(prof, dtype_name, flips, n_reps, W, B, esize, mode="search",
+                workload="icosidodecahedron_s1/2_M0_all10_B8"):
     """Roofline of the dominant kernel (packed H·v), per launch, HBM bound.
 
     Search path:  flips * (W*B*e + 20)       [every flipped state's segment, its record and bucket]
@@ -307,7 +309,8 @@ def hv_roofline(prof, dtype_name, flips, n_reps, W, B, esize, mode="search"):
         byt = flips * (seg + 20) + n_reps * (2 * seg + 16)
     peak = float(pk["hbm_gbs"]) * 1e9
     return {"bound": "hbm", "achieved": byt / t / 1e9, "peak": peak / 1e9, "unit": "GB/s", "frac": byt / t / peak,
-            "traffic": _traffic_record(dtype_name, mode), "algorithmic_per_launch": byt, "avg_launch_ms": t * 1e3,
+            "traffic": _traffic_record(dtype_name, mode, workload), "algorithmic_per_launch": byt,
+            "avg_launch_ms": t * 1e3,
             "flip_path": mode,
             "flips_per_launch": flips,
             "peak_source": f"{which} MEASURED_PEAKS.json hbm_gbs" if which == "measured" else "fallback 6.8 TB/s",
@@ -363,8 +366,9 @@ def cpu_baseline(budget_s=10.0):
                       f"processes x {busy:.1f} s (wall {wall:.1f} s including start-up)"}
 
 
-def hv_once():
-    """The profiling case: one packed H·v over all 10 blocks (FP32, B = 8) and one on the H_g block alone."""
+def hv_once(flips="search"):
+    """The profiling case: one packed H·v over all 10 blocks (FP32, B = 8) and one on the H_g block alone;
+    with flips="table" the sector's entry table is built first (one build-mode launch) and both H·v read it."""
     import torch
 
     from paper_2607_17429_gb300 import build as pb
@@ -377,6 +381,8 @@ def hv_once():
     c = cluster(CLUSTER)
     g = F.ftlm_group_init(c.gens, c.bonds)
     sec = F.ftlm_build_sector(g, TWO_S, TWO_M)
+    if flips == "table":
+        F.ftlm_sector_build_entries(sec)
     mb = F.ftlm_build_multiblock(sec, list(range(10)))
     rows = F.ftlm_multiblock_packed_rows(mb)
     gen = torch.Generator(device="cuda")
@@ -426,14 +432,40 @@ def config5(args):
     dim = F.ftlm_basis_info(blk)["dim"]
     out["dim"] = dim
     out["n_reps"] = F.ftlm_sector_info(sec)["n_reps"]
+    # FP32 run on the entry table when it fits beside the three vectors (else the search path);
+    # the FP64 run (three 29 GB vectors) always searches
+    flips32 = "search"
+    if args.flips == "table":
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out["entries"] = F.ftlm_sector_build_entries(sec, stream)
+            out["entries_build_s"] = time.perf_counter() - t0
+            flips32 = "table"
+        except F.FtlmError as e:
+            out["entries"] = f"not built: {e}"
+    out["config"]["flips_f32"] = FLIP_PATHS[flips32]
+    out["config"]["flips_f64"] = FLIP_PATHS["search"]
     res = {}
     for name, dt in (("f32", F.F32), ("f64", F.F64)):
+        if dt == F.F64 and flips32 == "table":
+            F.ftlm_sector_free_entries(sec)
         F.ftlm_profile_reset()
         F.ftlm_profile_enable(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        a, b, st = F.ftlm_lanczos(blk, dt, 1, N_STEPS, 4, 8, F.GAUSS, stream)
+        try:
+            a, b, st = F.ftlm_lanczos(blk, dt, 1, N_STEPS, 4, 8, F.GAUSS, stream)
+        except F.FtlmError as e:  # no room for the vectors beside the table: search path
+            if not (dt == F.F32 and flips32 == "table" and e.status == F.ENOMEM):
+                raise
+            F.ftlm_sector_free_entries(sec)
+            flips32 = "search"
+            out["config"]["flips_f32"] = FLIP_PATHS[flips32] + f" (the table left no room: {e})"
+            torch.cuda.synchronize()
+            e0.record(stream)
+            a, b, st = F.ftlm_lanczos(blk, dt, 1, N_STEPS, 4, 8, F.GAUSS, stream)
         e1.record(stream)
         torch.cuda.synchronize()
         F.ftlm_profile_enable(False)
@@ -443,12 +475,16 @@ def config5(args):
         res[name] = {"ms": ms, "steps": int(st[0]), "prof": prof, "thermo": th,
                      "hv_ms_per_launch": prof["hv_ms"] / max(1, prof["hv_launches"])}
     f32, f64 = res["f32"], res["f64"]
-    out["value"] = dim * f32["steps"] / (f32["ms"] / 1e3) / 1e9
+    # the FTLM step of the FP32 run includes its entry-table build
+    t_f32 = f32["ms"] / 1e3 + (out.get("entries_build_s", 0.0) if flips32 == "table" else 0.0)
+    out["value"] = dim * f32["steps"] / t_f32 / 1e9
     out["ms_lanczos_f32"] = f32["ms"]
     out["ms_lanczos_f64"] = f64["ms"]
     out["hv_ms_per_launch_f32"] = f32["hv_ms_per_launch"]
     out["hv_ms_per_launch_f64"] = f64["hv_ms_per_launch"]
-    out["roofline"] = hv_roofline(f32["prof"], "f32", 0, out["n_reps"], 5, 1, 4)
+    wl5 = "dodecahedron_s3/2_M0_Hg_B1"
+    out["roofline"] = hv_roofline(f32["prof"], "f32", 0, out["n_reps"], 5, 1, 4, flips32, wl5)
+    out["roofline_f64_search"] = hv_roofline(f64["prof"], "f64", 0, out["n_reps"], 5, 1, 8, "search", wl5)
     sel = T_GRID >= 0.05
     a32, a64 = f32["thermo"], f64["thermo"]
     out["E0_f32"], out["E0_f64"] = a32[4], a64[4]
@@ -456,6 +492,53 @@ def config5(args):
                             "max_dC_over_Cmax": float(np.abs(a32[2] - a64[2])[sel].max() / a64[2].max()),
                             "max_dlnZ_rel": float(np.abs((a32[0] - a64[0]) / a64[0]).max()),
                             "note": "one M = 0 block: C(T) of that block alone; chi is identically 0"}
+    print(json.dumps(out))
+
+
+def e0_dodecahedron(args):
+    """Cross-check against the paper's ground-state energy of the s=3/2 dodecahedron (Section 4.3:
+    E0 = -62.4388 from the M = 0 sector, FP32, 60 steps): every Gamma+- block of the spin-flip
+    M = 0 sector (G x Z_2), one FP32 Lanczos chain of `--e0-steps` steps each, on the sector's entry
+    table; E0 is the lowest Ritz value over the blocks."""
+    import torch
+
+    from paper_2607_17429_gb300 import build as pb
+
+    pb.build()
+    from paper_2607_17429_gb300 import ftlm as F
+    from workloads import cluster
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    c = cluster("dodecahedron")
+    g = F.ftlm_group_init(c.gens, c.bonds)
+    t0 = time.perf_counter()
+    sec = F.ftlm_build_sector_flip(g, 3, stream)
+    n_ent = F.ftlm_sector_build_entries(sec, stream)
+    torch.cuda.synchronize()
+    out = {"workload": "dodecahedron s=3/2, M=0, G x Z2 (240 elements), all 20 irrep blocks, R=1 Gaussian "
+                       f"(seed 4), {args.e0_steps} FP32 Lanczos steps per block, entry table",
+           "n_reps": F.ftlm_sector_info(sec)["n_reps"], "entries": n_ent, "prep_s": time.perf_counter() - t0,
+           "paper_E0": -62.4388, "blocks": []}
+    n_ir = F.ftlm_sector_symmetry(sec)["n_irreps"]
+    e0 = None
+    for k in range(n_ir):
+        blk = F.ftlm_build_block(sec, k, stream)
+        dim = F.ftlm_basis_info(blk)["dim"]
+        if dim == 0:
+            continue
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        a, b, st = F.ftlm_lanczos(blk, F.F32, 1, args.e0_steps, 4, 64 * 0 + k, F.GAUSS, stream)
+        th, w = F.ftlm_ritz(a, b, st)
+        ek = float(th[0, :st[0]].min())
+        out["blocks"].append({"irrep": k, "dim": dim, "E0": ek, "steps": int(st[0]),
+                              "s": time.perf_counter() - t1})
+        e0 = ek if e0 is None else min(e0, ek)
+        del blk
+    out["E0"] = e0
+    out["dE0_vs_paper"] = e0 - out["paper_E0"]
+    out["total_s"] = time.perf_counter() - t0
     print(json.dumps(out))
 
 
@@ -698,6 +781,9 @@ def main():
                     help="one packed 10-block H·v and one H_g-block H·v of the workload, then exit (profiling case)")
     ap.add_argument("--config5", action="store_true",
                     help="the largest single block instead: s=3/2 dodecahedron, M=0, H_g (3.6e9 states), R=1")
+    ap.add_argument("--e0-check", action="store_true",
+                    help="cross-check E0 of the s=3/2 dodecahedron against the paper (all M=0 Gamma+- blocks)")
+    ap.add_argument("--e0-steps", type=int, default=60)
     ap.add_argument("--config4", action="store_true",
                     help="serving loop: 2000 Poisson-arrival jobs over five systems under a 150 GB cap")
     ap.add_argument("--jobs", type=int, default=2000)
@@ -707,13 +793,16 @@ def main():
                     help="batched small blocks instead: every M>=0 sector x irrep of three clusters, R=24 Rademacher")
     args = ap.parse_args()
     if args.hv_once:
-        hv_once()
+        hv_once(args.flips)
         return
     if args.config5:
         config5(args)
         return
     if args.config4:
         config4(args)
+        return
+    if args.e0_check:
+        e0_dodecahedron(args)
         return
     if args.config3:
         config3(args)

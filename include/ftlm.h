@@ -138,8 +138,24 @@ void ftlm_group_free(ftlm_group *g);
  *         representatives), FTLM_ENOMEM, FTLM_ECUDA.
  */
 ftlm_status ftlm_build_sector(const ftlm_group *g, int two_s, int two_M, void *cuda_stream, ftlm_sector **out);
+/*
+ * The M = 0 sector under G x Z_2, Z_2 the global spin flip m -> -m (Section
+ * 2.2: at M = 0 the flip commutes with H and with the site permutations, and
+ * each irrep Gamma splits into Gamma+ and Gamma-, roughly halving the blocks).
+ * Element (g, z) has index g + z|G|; representatives are orbit minima under
+ * both; the flip image of a label is arithmetic (digits 2s - a_k), so the
+ * search adds no permutation.  The sector's irreps are Gamma_i+ at index 2i
+ * (rho(g, z) = rho_i(g)) and Gamma_i- at 2i + 1 (rho(g, z) = (-1)^z rho_i(g)),
+ * the canonical order of G x Z_2; blocks, packed sets, H·v, Lanczos and
+ * entry tables take these indices.  Errors as ftlm_build_sector, and
+ * FTLM_EINVAL when N s is not an integer (no M = 0 sector).
+ */
+ftlm_status ftlm_build_sector_flip(const ftlm_group *g, int two_s, void *cuda_stream, ftlm_sector **out);
 ftlm_status ftlm_sector_info(const ftlm_sector *s, uint64_t *n_reps, uint64_t *sector_dim, size_t *device_bytes);
-/* labels: [n_reps] packed labels; stab_mask: [n_reps][2] bit g of the 128-bit mask set when g fixes r. */
+/* The group acting on the sector: its order (|G|, or 2|G| with the spin flip), its irrep count and the flag. */
+ftlm_status ftlm_sector_symmetry(const ftlm_sector *s, int *order, int *n_irreps, int *flip);
+/* labels: [n_reps] packed labels; stab_mask: [n_reps][W] bit g of the mask set when element g fixes r,
+ * W = 2 words (128-bit masks) for a plain sector, 4 (256 bits, index g + z|G|) with the spin flip. */
 ftlm_status ftlm_sector_export(const ftlm_sector *s, uint64_t *labels, uint64_t *stab_mask);
 void ftlm_sector_free(ftlm_sector *s);
 
@@ -179,7 +195,7 @@ ftlm_status ftlm_build_basis(const ftlm_group *g, int two_s, int two_M, int irre
 ftlm_status ftlm_basis_info(const ftlm_basis *b, uint64_t *n_reps, uint64_t *dim, size_t *device_bytes);
 /*
  * Host copies for bit-exact tests (NULL = skip): labels [n_reps] packed,
- * stab_mask [n_reps][2], n_gamma [n_reps], offsets [n_reps + 1].
+ * stab_mask [n_reps][W] (W as in ftlm_sector_export), n_gamma [n_reps], offsets [n_reps + 1].
  */
 ftlm_status ftlm_basis_export(const ftlm_basis *b, uint64_t *labels, uint64_t *stab_mask, uint8_t *n_gamma,
                               uint64_t *offsets);

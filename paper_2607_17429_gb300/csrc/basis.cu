@@ -28,12 +28,12 @@ namespace {
 constexpr int kEnumThreads = 256;
 
 struct EnumArgs {
-    int N, bits, dmax, A, G;
+    int N, bits, dmax, A, G;  // G: elements acting on the sector (2|G| with the spin flip)
     uint64_t dim;          // sector dimension
     uint64_t chunk;        // labels per thread
     uint64_t n_threads;    // total threads
     const uint64_t *cnt;   // [(N+1)][(A+1)] ways for k low digits to sum to a
-    const uint8_t *src;    // [G][N] src[g][t] = pi_g^{-1}(t)
+    const uint8_t *src;    // [G][N] src[g][t] = pi_g^{-1}(t), + N when g also flips the spin
 };
 
 __device__ __forceinline__ unsigned digit(uint64_t n, int k, int bits, unsigned dmask) {
@@ -87,14 +87,15 @@ __device__ int rep_test(const EnumArgs &a, const uint8_t *src, uint64_t n, uint6
     int nontrivial = 0;
     if (mask) {
         mask[0] = 1;
-        mask[1] = 0;
+        mask[1] = mask[2] = mask[3] = 0;
     }
     for (int g = 1; g < a.G; ++g) {
         const uint8_t *s = src + g * a.N;
         int t = a.N - 1;
         unsigned u = 0, v = 0;
         for (; t >= 0; --t) {
-            u = digit(n, s[t], a.bits, dmask);
+            const int sk = s[t];
+            u = sk < a.N ? digit(n, sk, a.bits, dmask) : (unsigned)a.dmax - digit(n, sk - a.N, a.bits, dmask);
             v = digit(n, t, a.bits, dmask);
             if (u != v) break;
         }
@@ -139,7 +140,7 @@ __global__ void enum_write(EnumArgs a, const uint64_t *offsets, uint64_t *labels
     uint64_t pos = offsets[t];
     uint64_t r0 = t * a.chunk, r1 = min(r0 + a.chunk, a.dim);
     uint64_t n = unrank(a, r0);
-    uint64_t mask[2];
+    uint64_t mask[4];
     for (uint64_t r = r0; r < r1; ++r) {
         int k = rep_test(a, s_src, n, mask);
         if (k) {
@@ -147,9 +148,8 @@ __global__ void enum_write(EnumArgs a, const uint64_t *offsets, uint64_t *labels
             if (k == 2) {
                 unsigned long long q = atomicAdd(side_count, 1ull);
                 if (q < side_cap) {
-                    side[3 * q] = pos;
-                    side[3 * q + 1] = mask[0];
-                    side[3 * q + 2] = mask[1];
+                    side[5 * q] = pos;
+                    for (int w = 0; w < 4; ++w) side[5 * q + 1 + w] = mask[w];
                 }
             }
             ++pos;
@@ -158,21 +158,27 @@ __global__ void enum_write(EnumArgs a, const uint64_t *offsets, uint64_t *labels
     }
 }
 
+// masks as 4-word keys compared from the highest word down (the host sorts them the same way)
+__device__ __forceinline__ bool mask_less(const uint64_t *a, const uint64_t *b) {
+    for (int w = 3; w >= 0; --w)
+        if (a[w] != b[w]) return a[w] < b[w];
+    return false;
+}
+
 __global__ void assign_stab_ids(const uint64_t *side, uint64_t n_side, const uint64_t *masks, int n_masks,
                                 uint16_t *stab_id) {
     const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n_side) return;
-    const uint64_t m0 = side[3 * q + 1], m1 = side[3 * q + 2];
-    int lo = 0, hi = n_masks;  // masks sorted by (m1, m0)
+    const uint64_t *m = side + 5 * q + 1;
+    int lo = 0, hi = n_masks;
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
-        uint64_t a1 = masks[2 * mid + 1], a0 = masks[2 * mid];
-        if (a1 < m1 || (a1 == m1 && a0 < m0))
+        if (mask_less(masks + 4 * mid, m))
             lo = mid + 1;
         else
             hi = mid;
     }
-    stab_id[side[3 * q]] = (uint16_t)(lo + 1);
+    stab_id[side[5 * q]] = (uint16_t)(lo + 1);
 }
 
 __global__ void build_buckets(const uint64_t *labels, uint64_t n_reps, int shift, uint64_t n_buckets,
@@ -289,9 +295,48 @@ ftlm_status build_search_tables(ftlm_sector *s) {
     return FTLM_OK;
 }
 
-ftlm_status build_sector_impl(const GroupData &grp, int two_s, int two_M, cudaStream_t stream, ftlm_sector *s) {
-    const int N = grp.N, G = grp.G;
+// G x Z_2 (the spin flip at M = 0, Section 2.2) as a group acting on labels: element g + z|G| is
+// the signed permutation pi_g(k) + z N; irreps Gamma_i+ (2i: rho(g, z) = rho(g)) and Gamma_i-
+// (2i + 1: rho(g, z) = (-1)^z rho(g)), interleaved as the canonical irrep order puts them.
+GroupData spin_flip_extension(const GroupData &g) {
+    GroupData x = g;
+    const int G = g.G, N = g.N;
+    x.G = 2 * G;
+    x.perms.resize((size_t)2 * G * N);
+    for (size_t i = 0; i < (size_t)G * N; ++i) x.perms[(size_t)G * N + i] = g.perms[i] + N;
+    x.inv.resize(2 * G);
+    for (int i = 0; i < G; ++i) x.inv[G + i] = g.inv[i] + G;
+    x.mult.assign((size_t)4 * G * G, 0);
+    for (int z = 0; z < 2; ++z)
+        for (int w = 0; w < 2; ++w)
+            for (int i = 0; i < G; ++i)
+                for (int j = 0; j < G; ++j)
+                    x.mult[(size_t)(i + z * G) * 2 * G + (j + w * G)] = g.mult[(size_t)i * G + j] + (z ^ w) * G;
+    x.irreps.clear();
+    for (const Irrep &ir : g.irreps)
+        for (int sgn = 1; sgn >= -1; sgn -= 2) {
+            Irrep e;
+            e.dim = ir.dim;
+            e.fs = ir.fs;
+            e.chars.resize(2 * G);
+            for (int i = 0; i < G; ++i) e.chars[i] = ir.chars[i], e.chars[G + i] = sgn * ir.chars[i];
+            if (!ir.rho.empty()) {
+                const size_t dd = (size_t)ir.dim * ir.dim;
+                e.rho.resize(2 * G * dd);
+                for (size_t t = 0; t < G * dd; ++t) e.rho[t] = ir.rho[t], e.rho[G * dd + t] = sgn * ir.rho[t];
+            }
+            x.irreps.push_back(std::move(e));
+        }
+    return x;
+}
+
+ftlm_status build_sector_impl(const GroupData &grp_in, int two_s, int two_M, int flip, cudaStream_t stream,
+                              ftlm_sector *s) {
+    const int N = grp_in.N, G = grp_in.G;
     if (two_s < 1) return fail(FTLM_EINVAL, "two_s must be >= 1");
+    if (flip && two_M != 0) return fail(FTLM_EINVAL, "the spin flip is a symmetry of the M = 0 sector only");
+    const GroupData grp = flip ? spin_flip_extension(grp_in) : grp_in;
+    const int GX = grp.G;  // elements acting on labels
     if ((N * two_s + two_M) % 2) return fail(FTLM_EINVAL, "N s + M is not an integer");
     const int A = (N * two_s + two_M) / 2;
     if (A < 0 || A > N * two_s) return fail(FTLM_EINVAL, "M out of range");
@@ -306,7 +351,10 @@ ftlm_status build_sector_impl(const GroupData &grp, int two_s, int two_M, cudaSt
     s->N = N;
     s->G = G;
     s->A = A;
+    s->flip = flip;
     s->half = (two_s == 1 && N <= 32);
+    s->flipc = 0;
+    for (int k = 0; k < N; ++k) s->flipc |= (uint64_t)two_s << (bits * k);
     // counting table: cnt[k][a] = #strings of k digits (0..2s) with sum a
     std::vector<uint64_t> cnt((size_t)(N + 1) * (A + 1), 0);
     cnt[0] = 1;
@@ -317,9 +365,12 @@ ftlm_status build_sector_impl(const GroupData &grp, int two_s, int two_M, cudaSt
             cnt[(size_t)k * (A + 1) + a] = v;
         }
     s->sector_dim = cnt[(size_t)N * (A + 1) + A];
-    std::vector<uint8_t> src((size_t)G * N);
-    for (int g = 0; g < G; ++g)
-        for (int k = 0; k < N; ++k) src[(size_t)g * N + grp.perms[(size_t)g * N + k]] = (uint8_t)k;
+    std::vector<uint8_t> src((size_t)GX * N);
+    for (int g = 0; g < GX; ++g)
+        for (int k = 0; k < N; ++k) {
+            const int p = grp.perms[(size_t)g * N + k];  // >= N: the digit is also flipped
+            src[(size_t)g * N + (p % N)] = (uint8_t)(k + (p >= N ? N : 0));
+        }
     FTLM_CUDA(cudaMalloc((void **)&s->d_err, sizeof(int)));
     FTLM_CUDA(cudaMemset(s->d_err, 0, sizeof(int)));
     s->device_bytes += sizeof(int);
@@ -339,14 +390,14 @@ ftlm_status build_sector_impl(const GroupData &grp, int two_s, int two_M, cudaSt
     ea.bits = bits;
     ea.dmax = two_s;
     ea.A = A;
-    ea.G = G;
+    ea.G = GX;
     ea.dim = s->sector_dim;
     ea.chunk = s->sector_dim > (1ull << 32) ? 256 : 32;
     ea.n_threads = (s->sector_dim + ea.chunk - 1) / ea.chunk;
     ea.cnt = d_cnt.p;
     ea.src = d_src.p;
     const uint64_t n_blocks = (ea.n_threads + kEnumThreads - 1) / kEnumThreads;
-    const size_t smem = (size_t)G * N;
+    const size_t smem = (size_t)GX * N;
     DevBuf<uint32_t> counts;
     DevBuf<uint64_t> offsets;
     DevBuf<unsigned long long> nontriv;
@@ -372,35 +423,36 @@ ftlm_status build_sector_impl(const GroupData &grp, int two_s, int two_M, cudaSt
     s->device_bytes += n_reps * 10;
     FTLM_CUDA(cudaMemsetAsync(s->d_stab_id, 0, n_reps * 2, stream));
     DevBuf<uint64_t> side;
-    FTLM_CUDA(side.alloc(3 * n_side + 3));
+    FTLM_CUDA(side.alloc(5 * n_side + 5));
     FTLM_CUDA(cudaMemsetAsync(nontriv.p, 0, sizeof(unsigned long long), stream));
     count_launch();
     enum_write<<<(unsigned)n_blocks, kEnumThreads, smem, stream>>>(ea, offsets.p, s->d_labels, nontriv.p, side.p,
                                                                    n_side);
     FTLM_CUDA(cudaGetLastError());
     // stabilizer subgroups: dedupe masks on the host, ids ordered by mask
-    std::vector<uint64_t> h_side(3 * n_side);
+    std::vector<uint64_t> h_side(5 * n_side);
     if (n_side)
         FTLM_CUDA(cudaMemcpyAsync(h_side.data(), side.p, h_side.size() * 8, cudaMemcpyDeviceToHost, stream));
     FTLM_CUDA(cudaStreamSynchronize(stream));
-    std::vector<std::pair<uint64_t, uint64_t>> uniq;  // (m1, m0)
-    for (unsigned long long q = 0; q < n_side; ++q) uniq.emplace_back(h_side[3 * q + 2], h_side[3 * q + 1]);
+    std::vector<std::array<uint64_t, 4>> uniq;  // (m3, m2, m1, m0): the device's comparison order
+    for (unsigned long long q = 0; q < n_side; ++q)
+        uniq.push_back({h_side[5 * q + 4], h_side[5 * q + 3], h_side[5 * q + 2], h_side[5 * q + 1]});
     std::sort(uniq.begin(), uniq.end());
     uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
     if (uniq.size() + 1 > 65535) return fail(FTLM_EUNSUPPORTED, "too many stabilizer subgroups");
     s->stab_masks.clear();
     s->stab_elems.clear();
-    s->stab_masks.push_back({1ull, 0ull});
+    s->stab_masks.push_back({1ull, 0ull, 0ull, 0ull});
     s->stab_elems.push_back({0});
     std::vector<uint64_t> masks_flat;
     for (auto &u : uniq) {
-        s->stab_masks.push_back({u.second, u.first});
+        const std::array<uint64_t, 4> m = {u[3], u[2], u[1], u[0]};  // word w holds elements 64w..64w+63
+        s->stab_masks.push_back(m);
         std::vector<int> el;
-        for (int g = 0; g < G; ++g)
-            if (((g < 64 ? u.second : u.first) >> (g & 63)) & 1) el.push_back(g);
+        for (int g = 0; g < GX; ++g)
+            if ((m[g >> 6] >> (g & 63)) & 1) el.push_back(g);
         s->stab_elems.push_back(el);
-        masks_flat.push_back(u.second);
-        masks_flat.push_back(u.first);
+        for (int w = 0; w < 4; ++w) masks_flat.push_back(m[w]);
     }
     if (n_side) {
         DevBuf<uint64_t> d_masks;
@@ -637,13 +689,37 @@ ftlm_status ftlm_build_sector(const ftlm_group *g, int two_s, int two_M, void *c
     *out = nullptr;
     ftlm_sector *s = new (std::nothrow) ftlm_sector();
     if (!s) return fail(FTLM_ENOMEM, "host allocation failed");
-    ftlm_status st = build_sector_impl(g->d, two_s, two_M, (cudaStream_t)cuda_stream, s);
+    ftlm_status st = build_sector_impl(g->d, two_s, two_M, 0, (cudaStream_t)cuda_stream, s);
     if (st != FTLM_OK) {
         cudaStreamSynchronize((cudaStream_t)cuda_stream);
         free_sector(s);
         return st;
     }
     *out = s;
+    return FTLM_OK;
+}
+
+ftlm_status ftlm_build_sector_flip(const ftlm_group *g, int two_s, void *cuda_stream, ftlm_sector **out) {
+    if (!g || !out) return fail(FTLM_EINVAL, "NULL argument");
+    *out = nullptr;
+    if ((g->d.N * two_s) % 2) return fail(FTLM_EINVAL, "N s is not an integer: no M = 0 sector");
+    ftlm_sector *s = new (std::nothrow) ftlm_sector();
+    if (!s) return fail(FTLM_ENOMEM, "host allocation failed");
+    ftlm_status st = build_sector_impl(g->d, two_s, 0, 1, (cudaStream_t)cuda_stream, s);
+    if (st != FTLM_OK) {
+        cudaStreamSynchronize((cudaStream_t)cuda_stream);
+        free_sector(s);
+        return st;
+    }
+    *out = s;
+    return FTLM_OK;
+}
+
+ftlm_status ftlm_sector_symmetry(const ftlm_sector *s, int *order, int *n_irreps, int *flip) {
+    if (!s) return fail(FTLM_EINVAL, "sector is NULL");
+    if (order) *order = s->grp.G;
+    if (n_irreps) *n_irreps = (int)s->grp.irreps.size();
+    if (flip) *flip = s->flip;
     return FTLM_OK;
 }
 
@@ -659,12 +735,11 @@ ftlm_status ftlm_sector_export(const ftlm_sector *s, uint64_t *labels, uint64_t 
     if (!s) return fail(FTLM_EINVAL, "sector is NULL");
     if (labels) FTLM_CUDA(cudaMemcpy(labels, s->d_labels, s->n_reps * 8, cudaMemcpyDeviceToHost));
     if (stab_mask) {
+        const int W = s->flip ? 4 : 2;
         std::vector<uint16_t> ids(s->n_reps);
         FTLM_CUDA(cudaMemcpy(ids.data(), s->d_stab_id, s->n_reps * 2, cudaMemcpyDeviceToHost));
-        for (uint64_t i = 0; i < s->n_reps; ++i) {
-            stab_mask[2 * i] = s->stab_masks[ids[i]][0];
-            stab_mask[2 * i + 1] = s->stab_masks[ids[i]][1];
-        }
+        for (uint64_t i = 0; i < s->n_reps; ++i)
+            for (int w = 0; w < W; ++w) stab_mask[W * i + w] = s->stab_masks[ids[i]][w];
     }
     return FTLM_OK;
 }

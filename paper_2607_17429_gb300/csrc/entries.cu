@@ -80,6 +80,7 @@ ftlm_status entry_table_build(ftlm_sector *s, cudaStream_t stream) {
         ps.rows = n;
         ps.d_rec = rec.p;
         HvpPlan<float> plan;
+        plan.mode = 2;
         HvpArgs<float> &a = plan.a;
         hvp_fill_common<float>(s, &ps, 1, 4, a);
         a.err = err.p;

@@ -116,6 +116,9 @@ struct HvpPart {
 template <typename VT>
 struct HvpArgs {
     int N, G, n_bonds, bits, two_s, n_chunks;
+    int flip;                // G x Z_2 at M = 0: candidates U(g) a and their spin flips
+    unsigned long long flipc;  // flip(n) = n ^ flipc (s = 1/2) or flipc - n
+    unsigned neg;            // bit k: block k is a Gamma- block (rho(g, 1) = -rho(g))
     VT J;
     VT up[8], dn[8];         // sqrt(s(s+1) - m(m+1)), sqrt(s(s+1) - m(m-1)) per digit a = m + s
     const uint32_t *lut2;    // s = 1/2: [n_chunks][4][kMaxG] image of a 2-site chunk
@@ -596,12 +599,14 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                 }
                 LT my_rp = 0;
                 int my_g = 0;
-#pragma unroll 2
-                for (int j = 0; j < nround; ++j) {
+                // one flip's orbit minimum over the warp; FL: also the spin-flipped candidates
+                // (G x Z_2, elements (g, 1) after all of G: index 128 + g)
+                auto search = [&](int j, auto FL) {
                     const int e = __shfl_sync(kFullMask, my_e, j);
                     const int sg = HALF ? 1 : __shfl_sync(kFullMask, my_sg, j);
                     LT best = 0;
                     int bg = 0;
+                    LT cands[GPL];
 #pragma unroll
                     for (int c = 0; c < GPL; ++c) {
                         const int g = lane + 32 * c;
@@ -612,9 +617,20 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                             const LT dlt = s_dtab[e * kMaxG + g];
                             cand = sg > 0 ? I[c] + dlt : I[c] - dlt;
                         }
+                        cands[c] = cand;
                         if (c == 0 || cand < best) {
                             best = cand;
                             bg = g;
+                        }
+                    }
+                    if constexpr (decltype(FL)::value) {  // after all of G, in index order: strict <
+#pragma unroll
+                        for (int c = 0; c < GPL; ++c) {
+                            const LT cf = HALF ? (cands[c] ^ (LT)a.flipc) : ((LT)a.flipc - cands[c]);
+                            if (cf < best) {
+                                best = cf;
+                                bg = (lane + 32 * c) | 128;
+                            }
                         }
                     }
                     LT mn;
@@ -631,6 +647,12 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                         my_rp = mn;
                         my_g = gs;
                     }
+                };
+                if (!a.flip) {
+#pragma unroll 2
+                    for (int j = 0; j < nround; ++j) search(j, std::false_type{});
+                } else {
+                    for (int j = 0; j < nround; ++j) search(j, std::true_type{});
                 }
                 if (lane < nround) {
                     const uint64_t key = (uint64_t)my_rp;
@@ -675,7 +697,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                         }
                     } else {
                         f_off[base + lane] = off_f;
-                        f_sg[base + lane] = (sid_f << 8) | (uint32_t)my_g;  // my_g < |G| <= 128
+                        f_sg[base + lane] = (sid_f << 8) | (uint32_t)my_g;  // g* < |G| <= 128, bit 7: spin flip
                         f_c[base + lane] = my_c * __ldg(sqrtS + sid_f);      // c_a sqrt|Stab r'|
                     }
                 }
@@ -733,7 +755,8 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                 }
                 const int j = grp * Q + fg;
                 if (j < nf && b < B) {
-                    const int g_j = (int)(f_sg[j] & 255u);
+                    const int g_j = (int)(f_sg[j] & 127u);
+                    const unsigned negj = (f_sg[j] & 128u) ? a.neg : 0u;  // (g*, 1) in a Gamma- block: -rho(g*)
                     const VT cf = f_c[j];
                     const ST *xs = stage + (size_t)buf * a.stage_elems + (size_t)fg * a.slot_elems + b;
                     static_for<K>([&](auto kc) {
@@ -746,7 +769,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                         VT u[D];
 #pragma unroll
                         for (int g2 = 0; g2 < D; ++g2) u[g2] = st_get<VT, ST>(xs[(Zk + g2) * B]);
-                        hvp_rows<VT, D, RP>(R, u, cf, z + Zk);
+                        hvp_rows<VT, D, RP>(R, u, ((negj >> k) & 1u) ? -cf : cf, z + Zk);
                     });
                 }
                 __syncwarp();

@@ -33,7 +33,7 @@ struct HvpPlan {
     HvpArgs<VT> a;
     HvpGeom geo;
     const HvpOps<VT> *ops = nullptr;
-    int mode = 0;                     // 0: on-the-fly search; 1: entry table
+    int mode = 0;                     // 0: on-the-fly search; 1: entry table; 2: entry-table build
     uint64_t rows_total = 0;          // packed rows over all parts (profiling)
     std::vector<uint64_t> tile0, ntile;  // per part: first tile and tile count
 };

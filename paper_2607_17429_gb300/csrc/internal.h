@@ -61,6 +61,7 @@ struct PackedSet {
     int rho_total = 0, rho_totalf = 0;
     int rho_off[kPMaxK] = {}, rho_offf[kPMaxK] = {};
     std::vector<uint8_t> h_wtab;
+    uint32_t neg = 0;  // spin-flip sectors: bit k set when block k is a Gamma- block
     size_t device_bytes = 0;
 };
 
@@ -104,13 +105,18 @@ struct ftlm_group {
 // Packed-label sector on the device (basis.cu).
 struct ftlm_sector {
     std::atomic<int> refs{1};
+    // the group acting on the sector: G, or G x Z_2 with the spin flip at M = 0 (flip = 1), whose
+    // element g + z |G| is stored as the signed permutation pi_g(k) + z N and whose irreps are
+    // Gamma_i+ (2i) and Gamma_i- (2i + 1); G below is |G| of the site permutations alone
     ftlm::GroupData grp;
     int two_s = 0, two_M = 0, bits = 0, N = 0, G = 0, A = 0;
-    bool half = false;  // s = 1/2 with N <= 32: 32-bit labels, XOR flips
+    int flip = 0;
+    uint64_t flipc = 0;  // spin flip of a packed label: n ^ flipc (s = 1/2) or flipc - n (fields 2s - a_k)
+    bool half = false;   // s = 1/2 with N <= 32: 32-bit labels, XOR flips
     uint64_t n_reps = 0, sector_dim = 0;
     uint64_t *d_labels = nullptr;   // [n_reps] ascending packed labels
     uint16_t *d_stab_id = nullptr;  // [n_reps] stabilizer subgroup id (0 = trivial)
-    std::vector<std::array<uint64_t, 2>> stab_masks;  // per id
+    std::vector<std::array<uint64_t, 4>> stab_masks;  // per id: bit g of the group acting on the sector
     std::vector<std::vector<int>> stab_elems;         // per id
     uint32_t *d_bucket = nullptr;                     // [n_buckets + 1] first rep index of each bucket
     uint64_t *d_eoff = nullptr;                       // entry table (optional): [n_reps + 1] first entry

@@ -288,6 +288,7 @@ ftlm_status ftlm_lanczos(const ftlm_basis *b, ftlm_dtype dtype, int R, int n_ste
 ftlm_status ftlm_hv_multi(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, const void *const *x,
                           void *const *y, void *cuda_stream) {
     if (!mb || !x || !y) return fail(FTLM_EINVAL, "NULL argument");
+    if (mb->sec->flip) return fail(FTLM_EUNSUPPORTED, "spin-flip sectors run on the packed layout (ftlm_hv_packed)");
     if (B < 1 || B > kMaxB) return fail(FTLM_EINVAL, "B must be in 1..%d", kMaxB);
     for (int k = 0; k < mb->K; ++k)
         if (!x[k] || !y[k]) return fail(FTLM_EINVAL, "NULL vector for block %d", k);
@@ -315,6 +316,7 @@ ftlm_status ftlm_lanczos_multi(const ftlm_multiblock *mb, ftlm_dtype dtype, int 
             return lanczos_packed<float>(sets, R, n_steps, seed, rng, st, alpha, beta, steps_done, 2);
         return fail(FTLM_EINVAL, "unknown dtype");
     }
+    if (mb->sec->flip) return fail(FTLM_EUNSUPPORTED, "spin-flip sectors need a compiled packed block shape");
     if (dtype == FTLM_F64)
         return lanczos_multi_impl<double>(mb, R, n_steps, seed, block_ids, rng, st, alpha, beta, steps_done);
     if (dtype == FTLM_F32)

@@ -136,14 +136,14 @@ __global__ void __launch_bounds__(kLzThreads) lzp_start(const __grid_constant__ 
                     const uint64_t row0 = __ldg(P.boff[k] + rep);
                     VT v;
                     if (sid == 0) {
-                        v = (VT)start_value(row0 + (uint64_t)gam, a.chain0 + (uint32_t)b, a.key0, P.key1[k], a.rng);
+                        v = start_value_t<VT>(row0 + (uint64_t)gam, a.chain0 + (uint32_t)b, a.key0, P.key1[k], a.rng);
                     } else {  // lift the n_k(r) coefficients: V_k(r) x_k(r)
                         const int nk = __ldg(P.ntab + sid * K + k);
                         const VT *Vr = P.V[k] + ((size_t)sid * D + gam) * D;
                         v = (VT)0;
                         for (int q = 0; q < nk; ++q)
-                            v += __ldg(Vr + q) *
-                                 (VT)start_value(row0 + (uint64_t)q, a.chain0 + (uint32_t)b, a.key0, P.key1[k], a.rng);
+                            v += __ldg(Vr + q) * start_value_t<VT>(row0 + (uint64_t)q, a.chain0 + (uint32_t)b,
+                                                                   a.key0, P.key1[k], a.rng);
                     }
                     const ST sv = st_put<VT, ST>(v);
                     static_cast<ST *>(P.y)[e] = sv;

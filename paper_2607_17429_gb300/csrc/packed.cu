@@ -141,6 +141,8 @@ ftlm_status packed_set_build(ftlm_sector *s, int K, const ftlm_basis *const *blo
         ps->W += blocks[k]->d;
     }
     ps->shape = packed_shape_id(K, ps->dims);
+    for (int k = 0; k < K; ++k)
+        if (s->flip && (blocks[k]->irrep & 1)) ps->neg |= 1u << k;
     const size_t ns = s->stab_elems.size();
     std::vector<uint8_t> ntab(ns * K), wtab(ns);
     for (size_t t = 0; t < ns; ++t) {
@@ -255,6 +257,9 @@ void hvp_fill_common(const ftlm_sector *s, const PackedSet *ps, int B, int esize
         a.up[i] = (VT)(u > 0 ? sqrt(u) : 0.0);
         a.dn[i] = (VT)(dn > 0 ? sqrt(dn) : 0.0);
     }
+    a.flip = s->flip;
+    a.flipc = s->flipc;
+    a.neg = ps->neg;
     a.lut2 = s->d_lut2;
     a.pos = s->d_pos;
     a.dtab = s->d_dtab;
@@ -563,7 +568,7 @@ ftlm_status hvp_launch_plan(const HvpPlan<VT> &plan, double *dot_part, cudaStrea
     if (plan.a.n_tiles == 0) return FTLM_OK;
     HvpArgs<VT> a = plan.a;
     a.dot_part = dot_part;
-    a.flips = profiling_on() ? profile_flip_counter() : nullptr;
+    a.flips = profiling_on() && plan.mode != 2 ? profile_flip_counter() : nullptr;  // H·v flips only
     if (a.n_parts > 1 && !a.parts) return fail(FTLM_EINVAL, "several parts need a device descriptor array");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed) hv_timer_begin(stream, &e0, &e1);

@@ -38,4 +38,27 @@ __device__ __forceinline__ double start_value(uint64_t row, uint32_t chain, uint
     return sqrt(-2.0 * log(u1)) * cos(2.0 * M_PI * u2);
 }
 
+// The same draw for FP32 arithmetic (FP32 or FP16 vectors, which store it in
+// FP32 or less): the same Philox words and uniforms, Box–Muller evaluated in
+// FP32.  log(u1) is taken as log(u1) for u1 < 1/2 and as log1p(-(1 - u1)) with
+// the complement formed in FP64 otherwise, so no uniform loses its accuracy;
+// the result is within a few FP32 ulps of the FP64 draw.
+__device__ __forceinline__ float start_value_f32(uint64_t row, uint32_t chain, uint32_t k0, uint32_t k1, int rng) {
+    const U4 o = philox4x32_10(U4{(uint32_t)row, (uint32_t)(row >> 32), chain, 0u}, k0, k1);
+    if (rng == FTLM_RADEMACHER) return (o.x & 1u) ? -1.f : 1.f;
+    const uint64_t k = ((uint64_t)(o.x >> 5) << 26) | (o.y >> 6);  // u1 = (k + 1/2) 2^-53
+    const double u1 = ((double)k + 0.5) * 0x1p-53;
+    const float lg = u1 < 0.5 ? logf((float)u1) : log1pf(-(float)(((double)((1ull << 53) - k) - 0.5) * 0x1p-53));
+    const float u2 = (float)((double)(((uint64_t)(o.z >> 5) << 26) | (o.w >> 6)) * 0x1p-53);
+    return sqrtf(-2.f * lg) * cospif(2.f * u2);
+}
+
+template <typename VT>
+__device__ __forceinline__ VT start_value_t(uint64_t row, uint32_t chain, uint32_t k0, uint32_t k1, int rng) {
+    if constexpr (sizeof(VT) == 4)
+        return start_value_f32(row, chain, k0, k1, rng);
+    else
+        return start_value(row, chain, k0, k1, rng);
+}
+
 }  // namespace ftlm

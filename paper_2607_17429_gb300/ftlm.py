@@ -99,6 +99,8 @@ _SIGS = {
     "ftlm_autotune_report": [_P, ctypes.c_size_t],
     "ftlm_fill_label_keyed": [_P, _I, _I, _U64, _P, _P],
     "ftlm_basis_rows": [_P, _I, _P, _P, _P, _P],
+    "ftlm_build_sector_flip": [_P, _I, _P, _P],
+    "ftlm_sector_symmetry": [_P, _P, _P, _P],
     "ftlm_sector_build_entries": [_P, _P, _P],
     "ftlm_sector_free_entries": [_P],
     "ftlm_server_create": [ctypes.c_size_t, _I, _I, _P],
@@ -260,8 +262,9 @@ class Sector:
 
 
 class Basis:
-    def __init__(self, handle):
+    def __init__(self, handle, mask_words=2):
         self._h = handle
+        self.mask_words = mask_words  # 4 on spin-flip sectors (256-bit stabilizer masks)
 
     @property
     def handle(self):
@@ -279,6 +282,19 @@ def ftlm_build_sector(g: Group, two_s: int, two_M: int, stream=None) -> Sector:
     return Sector(h.value)
 
 
+def ftlm_build_sector_flip(g: Group, two_s: int, stream=None) -> Sector:
+    """M = 0 sector under G x Z_2 (spin flip); irreps 2i -> Gamma_i+, 2i + 1 -> Gamma_i-."""
+    h = ctypes.c_void_p()
+    _check(_lib.ftlm_build_sector_flip(g.handle, two_s, _stream(stream), ctypes.byref(h)))
+    return Sector(h.value)
+
+
+def ftlm_sector_symmetry(s: Sector) -> dict:
+    order, n_ir, flip = _I(), _I(), _I()
+    _check(_lib.ftlm_sector_symmetry(s.handle, ctypes.byref(order), ctypes.byref(n_ir), ctypes.byref(flip)))
+    return dict(order=order.value, n_irreps=n_ir.value, flip=flip.value)
+
+
 def ftlm_sector_info(s: Sector) -> dict:
     n, dim, nb = _U64(), _U64(), ctypes.c_size_t()
     _check(_lib.ftlm_sector_info(s.handle, ctypes.byref(n), ctypes.byref(dim), ctypes.byref(nb)))
@@ -288,7 +304,7 @@ def ftlm_sector_info(s: Sector) -> dict:
 def ftlm_sector_export(s: Sector):
     n = ftlm_sector_info(s)["n_reps"]
     labels = np.zeros(n, dtype=np.uint64)
-    masks = np.zeros((n, 2), dtype=np.uint64)
+    masks = np.zeros((n, 4 if ftlm_sector_symmetry(s)["flip"] else 2), dtype=np.uint64)
     _check(_lib.ftlm_sector_export(s.handle, _ptr(labels), _ptr(masks)))
     return labels, masks
 
@@ -307,7 +323,7 @@ def ftlm_sector_free_entries(s: Sector) -> None:
 def ftlm_build_block(s: Sector, irrep: int, stream=None) -> Basis:
     h = ctypes.c_void_p()
     _check(_lib.ftlm_build_block(s.handle, irrep, _stream(stream), ctypes.byref(h)))
-    return Basis(h.value)
+    return Basis(h.value, 4 if ftlm_sector_symmetry(s)["flip"] else 2)
 
 
 def ftlm_build_basis(g: Group, two_s: int, two_M: int, irrep: int, stream=None) -> Basis:
@@ -325,7 +341,7 @@ def ftlm_basis_info(b: Basis) -> dict:
 def ftlm_basis_export(b: Basis):
     n = ftlm_basis_info(b)["n_reps"]
     labels = np.zeros(n, dtype=np.uint64)
-    masks = np.zeros((n, 2), dtype=np.uint64)
+    masks = np.zeros((n, getattr(b, "mask_words", 2)), dtype=np.uint64)
     ng = np.zeros(n, dtype=np.uint8)
     off = np.zeros(n + 1, dtype=np.uint64)
     _check(_lib.ftlm_basis_export(b.handle, _ptr(labels), _ptr(masks), _ptr(ng), _ptr(off)))

@@ -68,6 +68,7 @@ def test_dodecahedron_s32_m0_hg_full_size():
     B, seed = 1, 5
     rows_ref = hv_rows_by_label(og, ir, c.bonds, 1.0, TWO_S, sample,
                                 lambda lab, n: label_keyed_values([lab], n, B, seed)[0])
+    idx = torch.from_numpy(np.concatenate([np.arange(f, f + n) for f, n in zip(first, nrows)])).cuda()
     for dt, tdt, tol in ((F.F32, torch.float32, 3e-5), (F.F64, torch.float64, 1e-12)):
         x = torch.empty((dim, B), dtype=tdt, device="cuda")
         F.ftlm_fill_label_keyed(blk, dt, B, seed, x)
@@ -75,7 +76,6 @@ def test_dodecahedron_s32_m0_hg_full_size():
         F.ftlm_hv(blk, dt, B, x, y)
         F.ftlm_basis_check(blk)
         del x
-        idx = torch.from_numpy(np.concatenate([np.arange(f, f + n) for f, n in zip(first, nrows)])).cuda()
         got = y[idx].double().cpu().numpy()
         del y
         torch.cuda.empty_cache()
@@ -87,3 +87,24 @@ def test_dodecahedron_s32_m0_hg_full_size():
                 continue
             assert np.abs(got[pos:pos + n] - r).max() <= tol * scale
             pos += n
+    # the entry table (2.5e10 flips x 8 bytes) reproduces the search path bitwise on the whole packed
+    # vector (FP16 storage keeps the two vectors and the table within the device: about 275 GB at the peak)
+    del blk
+    torch.cuda.empty_cache()
+    mb = F.ftlm_build_multiblock(sec, [ir])
+    rows = F.ftlm_multiblock_packed_rows(mb)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(6)
+    x = torch.randn((rows, 1), device="cuda", generator=gen, dtype=torch.float32).half()
+    y_search = torch.empty_like(x)
+    F.ftlm_hv_packed(mb, F.F16, 1, x, y_search)
+    F.ftlm_basis_check(F.ftlm_multiblock_block(mb, 0))
+    n_ent = F.ftlm_sector_build_entries(sec)
+    assert n_ent > 2e10
+    y_table = torch.empty_like(x)
+    F.ftlm_hv_packed(mb, F.F16, 1, x, y_table)
+    F.ftlm_basis_check(F.ftlm_multiblock_block(mb, 0))
+    assert torch.equal(y_search, y_table)
+    del x, y_search, y_table
+    F.ftlm_sector_free_entries(sec)
+    torch.cuda.empty_cache()
