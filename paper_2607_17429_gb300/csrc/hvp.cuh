@@ -285,32 +285,45 @@ __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsig
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 // z[beta] += cf * sum_gamma R[gamma * RP + beta] u[gamma] for beta < D.  FP32 with
 // D >= 2 runs pairs of output rows through fma.f32x2 (rows of R padded to RP,
 // an even count); otherwise scalar FMAs.  Same products and summation order
-// over gamma either way.
+// over gamma either way (the first product is a multiply, as a fused
+// multiply-add onto zero would round it).
 template <typename VT, int D, int RP>
 __device__ __forceinline__ void hvp_rows(const VT *__restrict__ R, const VT (&u)[D], VT cf, VT *z) {
     if constexpr (sizeof(VT) == 4 && D >= 2) {
         constexpr int NP = (D + 1) / 2;
         unsigned long long acc[NP];
 #pragma unroll
-        for (int q = 0; q < NP; ++q) acc[q] = 0ull;  // (+0.0f, +0.0f)
-#pragma unroll
         for (int ga = 0; ga < D; ++ga) {
             VT row[RP];
             load_row<VT, RP>(R + ga * RP, row);
             const unsigned long long uu = f2_pack(u[ga], u[ga]);
 #pragma unroll
-            for (int q = 0; q < NP; ++q) acc[q] = f2_fma(f2_pack(row[2 * q], row[2 * q + 1]), uu, acc[q]);
+            for (int q = 0; q < NP; ++q) {
+                const unsigned long long rr = f2_pack(row[2 * q], row[2 * q + 1]);
+                acc[q] = ga == 0 ? f2_mul(rr, uu) : f2_fma(rr, uu, acc[q]);
+            }
         }
+        const unsigned long long cc = f2_pack(cf, cf);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
+        for (int q = 0; q < D / 2; ++q) {  // z pairs += cf * acc, the same FMA per element
             float lo, hi;
-            f2_unpack(acc[q], lo, hi);
-            z[2 * q] += cf * lo;
-            if (2 * q + 1 < D) z[2 * q + 1] += cf * hi;
+            f2_unpack(f2_fma(acc[q], cc, f2_pack(z[2 * q], z[2 * q + 1])), lo, hi);
+            z[2 * q] = lo;
+            z[2 * q + 1] = hi;
+        }
+        if constexpr (D % 2) {
+            float lo, hi;
+            f2_unpack(acc[NP - 1], lo, hi);
+            z[D - 1] += cf * lo;
         }
     } else {
         VT acc[D];

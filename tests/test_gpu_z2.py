@@ -144,3 +144,20 @@ def test_flip_spectra_union_is_the_parent_spectrum():
             assert len(ev) == len(ref) and np.abs(ev - ref).max() < 1e-10 * max(1.0, np.abs(ref).max())
             checked += 1
     assert checked >= 12
+
+
+def test_flip_sector_full_size_dodecahedron_block_dims():
+    """The s=3/2 dodecahedron's M = 0 sector under G x Z_2 (3.6e8 representatives): every Gamma+-
+    block dimension equals the oracle's character formula, and each pair adds up to Table 2."""
+    torch_cuda()
+    F = ftlm()
+    from oracle.sector import block_dims
+
+    g = product_group("dodecahedron")
+    og = oracle_group("dodecahedron")
+    ref = block_dims(SpinFlipExtended(og), 3, 0)
+    sec = F.ftlm_build_sector_flip(g, 3)
+    for k in range(2 * len(og.irreps)):
+        blk = F.ftlm_build_block(sec, k)
+        assert F.ftlm_basis_info(blk)["dim"] == ref[k], k
+        del blk

@@ -72,7 +72,7 @@ def test_z2_dense_check_flip_parity_and_spectra(name, two_s):
             assert np.abs(np.sort(ev) - np.linalg.eigvalsh(parent.dense())).max() < 1e-10
 
 
-@pytest.mark.parametrize("name,two_s", CASES + [("icosahedron", 3), ("dodecahedron", 1)])
+@pytest.mark.parametrize("name,two_s", CASES + [("icosahedron", 3), ("dodecahedron", 1), ("dodecahedron", 3)])
 def test_z2_block_dims_character_formula(name, two_s):
     c = cluster(name)
     g = Group(c.gens, c.bonds)
@@ -125,3 +125,18 @@ def test_z2_flip_check_catches_wrong_sign():
         return  # the character count and the projector rank disagree: caught
     Psi = projected_basis(blk, labels)
     assert blk.dim == 0 or np.abs(Fm @ Psi + Psi).max() > 1e-3
+
+
+def test_z2_split_of_table2():
+    """Table 2 lists the s=3/2 dodecahedron's M = 0 blocks with the Gamma+- sub-blocks added back
+    (Section 4.3): the character formula over G x Z_2 splits every entry into two parts."""
+    import os
+
+    c = cluster("dodecahedron")
+    g = Group(c.gens, c.bonds)
+    dimsx = block_dims(SpinFlipExtended(g), 3, 0)
+    sums = sorted(dimsx[2 * i] + dimsx[2 * i + 1] for i in range(len(g.irreps)))
+    path = os.path.join(os.path.dirname(__file__), "golden", "table2_dodecahedron_s32_M0.txt")
+    table = sorted(int(ln.split()[3]) for ln in open(path) if ln.strip() and not ln.startswith("#"))
+    assert sums == table
+    assert all(dimsx[k] > 0 for k in range(len(dimsx)))
