@@ -437,6 +437,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
     for (int k = 0; k < K; ++k) dacc[k].zero();
     const bool want_dot = a.dot_part != nullptr;
     int cur_part = -1;
+    unsigned long long n_flips = 0;  // profiling: flips of this warp, one atomic at the end
 
     // CTA-wide flush of the per-lane dot accumulators into the partials of part p
     auto flush = [&](int p) {
@@ -530,7 +531,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                 diag = a.J * (VT)diag4 * (VT)0.25;
                 const uint64_t e0 = __ldg(P.eoff + rep);
                 nf = (int)(__ldg(P.eoff + rep + 1) - e0);
-                if (a.flips && lane == 0) atomicAdd(a.flips, (unsigned long long)nf);
+                n_flips += (unsigned long long)nf;
                 for (int base = lane; base < nf; base += 32) {
                     const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(P.ent + e0 + base));
                     const uint32_t tgt = raw.x, g8 = raw.y & 255u, es = (raw.y >> 8) & 255u, sidf = raw.y >> 16;
@@ -583,7 +584,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
             diag4 = __reduce_add_sync(kFullMask, diag4);
             diag = a.J * (VT)diag4 * (VT)0.25;
             nf = __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]);
-            if (a.flips && lane == 0) atomicAdd(a.flips, (unsigned long long)nf);
+            n_flips += (unsigned long long)nf;
             if (MODE == 2 && lane == 0 && (uint64_t)nf != P.eoff[rep + 1] - P.eoff[rep])
                 atomicOr(a.err, kErrMissingRep);  // the count pass and the kernel disagree
 
@@ -846,6 +847,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
         }
     }
     if (want_dot && cur_part >= 0) flush(cur_part);
+    if (a.flips && lane == 0 && n_flips) atomicAdd(a.flips, n_flips);
 }
 
 // ---------------------------------------------------------------- host side

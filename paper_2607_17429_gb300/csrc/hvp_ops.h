@@ -3,7 +3,7 @@
 
 #include <vector>
 
-#include "hvp.cuh"
+#include "hvp_lane.cuh"
 
 namespace ftlm {
 
@@ -19,13 +19,17 @@ struct HvpOps {
     int (*occupancy)(const HvpArgs<VT> &, int warps, int nbuf);
     ftlm_status (*launch)(HvpArgs<VT>, const HvpGeom &, cudaStream_t);
     int max_threads;
+    int tile_fixed;  // representatives per tile fixed by the kernel (0: chosen with the geometry)
 };
 
 #define FTLM_HVP_OPS_M(VT, ST, SH, GPL, HALF, MODE)                                              \
     HvpOps<VT> {                                                                                   \
         &hvp_occupancy_t<VT, ST, SH, GPL, HALF, MODE>, &hvp_launch_t<VT, ST, SH, GPL, HALF, MODE>, \
-            hvp_max_threads<VT, SH>()                                                              \
+            hvp_max_threads<VT, SH>(), 0                                                           \
     }
+// one thread per representative (table mode, one block, B = 1; hvp_lane.cuh)
+#define FTLM_HVP_LANE_OPS(VT, ST, D) \
+    HvpOps<VT> { &hvp_lane_occupancy_t<VT, ST, D>, &hvp_lane_launch_t<VT, ST, D>, kLaneThreads, kLaneThreads }
 #define FTLM_HVP_OPS(VT, ST, SH, GPL, HALF) FTLM_HVP_OPS_M(VT, ST, SH, GPL, HALF, 0)
 
 template <typename VT>
@@ -70,6 +74,10 @@ const HvpOps<float> *hvp_ops_multi_f16(int shape, int gpl, bool half);
 const HvpOps<double> *hvp_ops_table_f64(int shape);
 const HvpOps<float> *hvp_ops_table_f32(int shape);
 const HvpOps<float> *hvp_ops_table_f16(int shape);
+// table mode, one thread per representative: single blocks (shape D1..D5) at B = 1
+const HvpOps<double> *hvp_ops_lane_f64(int shape);
+const HvpOps<float> *hvp_ops_lane_f32(int shape);
+const HvpOps<float> *hvp_ops_lane_f16(int shape);
 // build mode (writes the entry table; no gathers or outputs)
 const HvpOps<float> *hvp_ops_build(int gpl, bool half);
 

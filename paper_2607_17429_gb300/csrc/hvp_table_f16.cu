@@ -14,4 +14,12 @@ const HvpOps<float> *hvp_ops_table_f16(int shape) {
     return &tab[shape];
 }
 
+const HvpOps<float> *hvp_ops_lane_f16(int shape) {
+    static const HvpOps<float> tab[5] = {FTLM_HVP_LANE_OPS(float, __half, 1), FTLM_HVP_LANE_OPS(float, __half, 2),
+                                       FTLM_HVP_LANE_OPS(float, __half, 3), FTLM_HVP_LANE_OPS(float, __half, 4),
+                                       FTLM_HVP_LANE_OPS(float, __half, 5)};
+    if (shape < kShapeD1 || shape > kShapeD5) return nullptr;
+    return &tab[shape - kShapeD1];
+}
+
 }  // namespace ftlm

@@ -14,4 +14,12 @@ const HvpOps<double> *hvp_ops_table_f64(int shape) {
     return &tab[shape];
 }
 
+const HvpOps<double> *hvp_ops_lane_f64(int shape) {
+    static const HvpOps<double> tab[5] = {FTLM_HVP_LANE_OPS(double, double, 1), FTLM_HVP_LANE_OPS(double, double, 2),
+                                       FTLM_HVP_LANE_OPS(double, double, 3), FTLM_HVP_LANE_OPS(double, double, 4),
+                                       FTLM_HVP_LANE_OPS(double, double, 5)};
+    if (shape < kShapeD1 || shape > kShapeD5) return nullptr;
+    return &tab[shape - kShapeD1];
+}
+
 }  // namespace ftlm

@@ -368,7 +368,7 @@ ftlm_status hvp_choose_geom(const HvpOps<VT> *ops, HvpArgs<VT> a, bool tma, HvpG
                     geo.tma = tma ? 1 : 0;
                     geo.rho_smem = rho;
                     geo.own = own;
-                    geo.tile_reps = warps * 4;
+                    geo.tile_reps = ops->tile_fixed ? ops->tile_fixed : warps * 4;
                     geo.grid = sms * per_sm;
                     return FTLM_OK;
                 }
@@ -521,6 +521,14 @@ ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpP
     for (auto &p : parts) mode = mode && p.eoff && p.ent;
     plan.mode = mode;
     plan.ops = hvp_ops<VT>(ps->shape, gpl, s->half, esize, mode);
+    if (mode == 1 && ps->K == 1 && B == 1) {  // one thread per representative
+        const HvpOps<VT> *lane = nullptr;
+        if constexpr (sizeof(VT) == 8)
+            lane = hvp_ops_lane_f64(ps->shape);
+        else
+            lane = esize == 2 ? hvp_ops_lane_f16(ps->shape) : hvp_ops_lane_f32(ps->shape);
+        if (lane) plan.ops = lane;
+    }
     if (!plan.ops)
         return fail(FTLM_EUNSUPPORTED, "no compiled packed kernel for shape %d with |G| = %d", ps->shape, s->G);
     bool tma = (B * esize) % 16 == 0;
@@ -534,7 +542,7 @@ ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpP
     ftlm_status st = hvp_choose_geom<VT>(plan.ops, a, tma, plan.geo);
     if (st != FTLM_OK) return st;
     plan.rows_total = 0;
-    if (g_autotune.load() && !getenv("FTLM_HV_WARPS") && !getenv("FTLM_HV_NBUF")) {
+    if (g_autotune.load() && !plan.ops->tile_fixed && !getenv("FTLM_HV_WARPS") && !getenv("FTLM_HV_NBUF")) {
         int lg = 0;
         while ((1ull << lg) < n_reps_total) ++lg;
         const TuneKey key{ps->shape, gpl, s->half ? 1 : 0, esize, B, tma ? 1 : 0, lg, mode};

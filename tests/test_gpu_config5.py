@@ -87,8 +87,10 @@ def test_dodecahedron_s32_m0_hg_full_size():
                 continue
             assert np.abs(got[pos:pos + n] - r).max() <= tol * scale
             pos += n
-    # the entry table (2.5e10 flips x 8 bytes) reproduces the search path bitwise on the whole packed
-    # vector (FP16 storage keeps the two vectors and the table within the device: about 275 GB at the peak)
+    # the entry table (2.5e10 flips x 8 bytes) reproduces the search path on the whole packed vector
+    # (FP16 storage keeps the two vectors and the table within the device: about 275 GB at the peak);
+    # at B = 1 the table path runs one thread per representative and sums the flips in entry order,
+    # so the FP32 sums differ in rounding and the FP16 outputs by at most one FP16 rounding step
     del blk
     torch.cuda.empty_cache()
     mb = F.ftlm_build_multiblock(sec, [ir])
@@ -104,7 +106,11 @@ def test_dodecahedron_s32_m0_hg_full_size():
     y_table = torch.empty_like(x)
     F.ftlm_hv_packed(mb, F.F16, 1, x, y_table)
     F.ftlm_basis_check(F.ftlm_multiblock_block(mb, 0))
-    assert torch.equal(y_search, y_table)
-    del x, y_search, y_table
     F.ftlm_sector_free_entries(sec)
+    del x
+    for c0 in range(0, rows, 1 << 28):  # compared in chunks: FP32 copies of the whole vectors do not fit
+        ys = y_search[c0:c0 + (1 << 28)].float()
+        yt = y_table[c0:c0 + (1 << 28)].float()
+        assert bool(((ys - yt).abs() <= 2.0 ** -10 * ys.abs() + 1e-6).all())
+    del y_search, y_table, ys, yt
     torch.cuda.empty_cache()
