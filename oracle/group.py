@@ -12,10 +12,22 @@ Conventions (shared with the library only as documented conventions, not code):
   so the trivial irrep is first.
 
 The character table comes from the class algebra (the class-sum structure
-constants have the central characters as common eigenvectors); every irrep of
-real Frobenius-Schur type is then realised as an orthogonal representation by
-projecting the left regular representation onto its isotypic component and
-splitting that with a random symmetric element of the right-regular commutant.
+constants have the central characters as common eigenvectors).  The irreps are
+then taken over the reals (Section 3 keeps real arithmetic for irreps of real
+Frobenius-Schur type; the real form here extends that to the other two types):
+
+* real type (indicator +1): the irrep itself, chi_R = chi;
+* complex type (indicator 0): one entry for the pair Gamma, conj(Gamma), the real
+  representation of dimension 2 d_Gamma with chi_R = chi + conj(chi);
+* quaternionic type (indicator -1): the real representation of dimension
+  2 d_Gamma with chi_R = 2 chi.
+
+Each is realised as an orthogonal representation by projecting the left regular
+representation onto its real isotypic component and splitting that with a
+random symmetric element of the right-regular commutant.  kappa = <chi_R, chi_R>
+(1, 2, 4) is the dimension of the real commutant; a single-partner-row block of
+the real form counts every level kappa times its multiplicity in one complex
+irrep copy, so its FTLM weight (Eq. 5's d_Gamma) is dim / kappa.
 """
 from __future__ import annotations
 
@@ -53,12 +65,24 @@ def close_group(gens, max_order=100000):
     return np.array(sorted(seen), dtype=np.int32)
 
 
+KAPPA = {1: 1, 0: 2, -1: 4}  # Frobenius-Schur indicator -> <chi_R, chi_R>
+
+
 @dataclasses.dataclass
 class Irrep:
-    dim: int
-    fs: int  # Frobenius-Schur indicator
-    chars: np.ndarray  # [G]
-    rho: np.ndarray | None  # [G, d, d] real orthogonal, None if not of real type
+    dim: int  # dimension of the real representation
+    fs: int  # Frobenius-Schur indicator of its complex constituent
+    chars: np.ndarray  # [G], chi_R
+    rho: np.ndarray | None  # [G, d, d] real orthogonal
+
+    @property
+    def kappa(self) -> int:
+        return KAPPA[self.fs]
+
+    @property
+    def weight(self) -> int:
+        """The block's multiplicity factor in Eqs. 5, 6 and 14 (d_Gamma for real type)."""
+        return self.dim // self.kappa
 
 
 class Group:
@@ -126,11 +150,34 @@ class Group:
             chi_cls = d * w / size
             chars.append(chi_cls)
         chars = np.array(chars)
-        if np.max(np.abs(chars.imag)) > 1e-8:
-            raise NotImplementedError("complex characters are outside the oracle's real path")
-        chars = chars.real
-        self.class_chars = chars  # [n_irreps, K]
+        # Frobenius-Schur indicator (1/|G|) sum_g chi(g^2), by classes
+        sq = np.array([self.class_of[self.mult[c[0], c[0]]] for c in self.classes])
+        real_forms, fss, used = [], [], set()
+        for t in range(K):
+            if t in used:
+                continue
+            chi = chars[t]
+            nu = float(np.real(np.sum(size * chi[sq])) / G)
+            fs = int(round(nu))
+            if abs(nu - fs) > 1e-6 or fs not in KAPPA:
+                raise ArithmeticError("Frobenius-Schur indicator is not 1, 0 or -1")
+            if fs == 0:
+                conj = [u for u in range(K) if u != t and u not in used
+                        and np.max(np.abs(chars[u] - np.conj(chi))) < 1e-8]
+                if len(conj) != 1:
+                    raise ArithmeticError("complex character without its conjugate")
+                used.add(conj[0])
+                real_forms.append(2.0 * chi.real)
+            elif np.max(np.abs(chi.imag)) > 1e-8:
+                raise ArithmeticError("character of real or quaternionic type is not real")
+            else:
+                real_forms.append((1.0 if fs == 1 else 2.0) * chi.real)
+            used.add(t)
+            fss.append(fs)
+        chars = np.array(real_forms)
+        self.class_chars = chars  # [n_irreps, K], chi_R by class
         self.char_table = chars[:, self.class_of]  # [n_irreps, G]
+        self._fs = fss
 
     # ---- real irreps ------------------------------------------------------
     def _regular(self, g):
@@ -146,21 +193,22 @@ class Group:
         X = self.mult[self.inv][:, :]  # X[x, y] = x^{-1} y
         S = cvec[X] + cvec[X.T]
         irreps = []
-        for chi in self.char_table:
+        for chi, fs in zip(self.char_table, self._fs):
             d = int(round(chi[0]))
-            fs = int(round(np.sum(chi[self.mult[np.arange(G), np.arange(G)]]) / G))
-            if fs != 1:
-                irreps.append(Irrep(d, fs, chi.copy(), None))
-                continue
-            # isotypic projector E[x, y] = (d/|G|) chi(x y^{-1})
-            E = (d / G) * chi[self.mult[np.arange(G)[:, None], self.inv[None, :]]]
+            kappa = KAPPA[fs]
+            # real isotypic projector E[x, y] = (d / (kappa |G|)) chi_R(x y^{-1}), rank d^2 / kappa
+            E = (d / (kappa * G)) * chi[self.mult[np.arange(G)[:, None], self.inv[None, :]]]
             ev, U = np.linalg.eigh(E)
             W = U[:, ev > 0.5]
-            if W.shape[1] != d * d:
+            if W.shape[1] * kappa != d * d:
                 raise RuntimeError("isotypic component has the wrong dimension")
+            # the commutant acts on W as a symmetric matrix over R, C or H: every eigenvalue
+            # of a generic one has multiplicity d (one copy of the real irreducible)
             lam, Q = np.linalg.eigh(W.T @ S @ W)
-            if d > 1 and not (lam[d - 1] - lam[0] < 1e-8 * (1 + abs(lam).max())
-                              and lam[d] - lam[d - 1] > 1e-6 * (1 + abs(lam).max())):
+            tol = 1 + abs(lam).max()
+            if d > 1 and lam[d - 1] - lam[0] > 1e-8 * tol:
+                raise RuntimeError("commutant split did not isolate one irreducible copy")
+            if W.shape[1] > d and lam[d] - lam[d - 1] < 1e-6 * tol:
                 raise RuntimeError("commutant split did not isolate one irreducible copy")
             Bm = W @ Q[:, :d]
             rho = np.empty((G, d, d))
@@ -179,8 +227,6 @@ class Group:
         G = self.order
         res = {"hom": 0.0, "orth": 0.0, "char": 0.0}
         for ir in self.irreps:
-            if ir.rho is None:
-                continue
             r = ir.rho
             prod = np.einsum("gab,hbc->ghac", r, r)
             res["hom"] = max(res["hom"], float(np.max(np.abs(prod - r[self.mult]))))
@@ -188,8 +234,10 @@ class Group:
                 np.einsum("gab,gcb->gac", r, r) - np.eye(ir.dim)[None]))))
             res["char"] = max(res["char"], float(np.max(np.abs(np.trace(r, axis1=1, axis2=2) - ir.chars))))
         ct = self.char_table
-        res["row_orth"] = float(np.max(np.abs(ct @ ct.T / G - np.eye(len(ct)))))
-        res["sum_d2"] = int(sum(ir.dim ** 2 for ir in self.irreps))
+        kap = np.diag([ir.kappa for ir in self.irreps])
+        res["row_orth"] = float(np.max(np.abs(ct @ ct.T / G - kap)))
+        # sum over the complex irreps of d^2: a complex pair gives 2 (d/2)^2, a quaternionic one (d/2)^2
+        res["sum_d2"] = int(sum(ir.dim ** 2 // ir.kappa for ir in self.irreps))
         return res
 
     def element(self, perm):
@@ -220,6 +268,6 @@ class SpinFlipExtended:
         self.irreps = []
         for ir in group.irreps:
             for sgn in (1.0, -1.0):
-                rho = None if ir.rho is None else np.concatenate([ir.rho, sgn * ir.rho])
+                rho = np.concatenate([ir.rho, sgn * ir.rho])
                 self.irreps.append(Irrep(ir.dim, ir.fs, np.concatenate([ir.chars, sgn * ir.chars]), rho))
         self.char_table = np.array([ir.chars for ir in self.irreps])

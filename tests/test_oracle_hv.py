@@ -100,7 +100,7 @@ def _all_block_spectra(name, two_s):
             assert np.abs(Hb - Hb.T).max() < 1e-12
             e = np.linalg.eigvalsh(Hb)
             spec[(two_M, ir)] = e
-            evs.extend(list(e) * (mult * g.irreps[ir].dim))
+            evs.extend(list(e) * (mult * g.irreps[ir].weight))
     return c, g, np.sort(np.array(evs)), spec
 
 

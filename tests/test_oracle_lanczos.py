@@ -85,7 +85,7 @@ def _exact_blocks(name, two_s):
             if blk.dim == 0:
                 continue
             e = np.linalg.eigvalsh(blk.dense())
-            blocks.append(dict(two_M=two_M, d_gamma=g.irreps[ir].dim, dim=blk.dim, R=blk.dim,
+            blocks.append(dict(two_M=two_M, d_gamma=g.irreps[ir].weight, dim=blk.dim, R=blk.dim,
                                alpha=[np.array([v]) for v in e], beta=[np.array([0.0]) for _ in e]))
     return c, blocks
 

@@ -128,6 +128,73 @@ def _ring(n):
     return Cluster(f"ring:{n}", n, b, np.stack([rot, ref]))
 
 
+def _chain(n):
+    """n-site ring with its translations only (the cyclic group C_n: irreps of complex type for
+    momenta k != 0, pi)."""
+    if n < 3:
+        raise ValueError("chain needs at least 3 sites")
+    rot = np.array([(k + 1) % n for k in range(n)], dtype=np.int32)
+    b = np.array(sorted(tuple(sorted((k, (k + 1) % n))) for k in range(n)), dtype=np.int32)
+    return Cluster(f"chain:{n}", n, b, rot[None, :])
+
+
+def _tetrahedron_rotations():
+    """The tetrahedron with its rotation group T (order 12; one pair of complex-type irreps)."""
+    V = np.array([(1.0, 1.0, 1.0), (1.0, -1.0, -1.0), (-1.0, 1.0, -1.0), (-1.0, -1.0, 1.0)])
+    c3 = _rot((1.0, 1.0, 1.0), 2 * math.pi / 3)
+    c2 = _rot((0.0, 0.0, 1.0), math.pi)
+    gens = np.stack([_perm_from_matrix(M, V) for M in (c3, c2)])
+    return Cluster("tetrahedron:t", 4, _nn_bonds(V), gens, V)
+
+
+def _complete(p):
+    """Complete graph on p sites (p prime) with the affine group x -> a x + b (mod p), a != 0:
+    order p(p - 1), irreps of dimension 1 (some of complex type) and one of dimension p - 1."""
+    if p < 3 or any(p % q == 0 for q in range(2, int(p ** 0.5) + 1)):
+        raise ValueError("complete:p needs a prime p >= 3")
+    root = next(a for a in range(2, p) if len({pow(a, e, p) for e in range(1, p)}) == p - 1)
+    shift = np.array([(x + 1) % p for x in range(p)], dtype=np.int32)
+    scale = np.array([(root * x) % p for x in range(p)], dtype=np.int32)
+    b = np.array([(i, j) for i in range(p) for j in range(i + 1, p)], dtype=np.int32)
+    return Cluster(f"complete:{p}", p, b, np.stack([shift, scale]))
+
+
+def _petersen():
+    """Petersen graph: sites are the 2-subsets of {0..4}, bonds join disjoint subsets; the group
+    is S_5 acting on the subsets (order 120, irreps up to dimension 6)."""
+    sub = [(a, b) for a in range(5) for b in range(a + 1, 5)]
+    index = {t: i for i, t in enumerate(sub)}
+
+    def perm(f):
+        return np.array([index[tuple(sorted((f[a], f[b])))] for a, b in sub], dtype=np.int32)
+
+    gens = np.stack([perm([1, 2, 3, 4, 0]), perm([1, 0, 2, 3, 4])])
+    bonds = np.array([(i, j) for i in range(10) for j in range(i + 1, 10) if not set(sub[i]) & set(sub[j])],
+                     dtype=np.int32)
+    return Cluster("petersen", 10, bonds, gens)
+
+
+def _q8():
+    """Cayley graph of the quaternion group Q_8 with connection set {+-i, +-j}; the group acts by
+    left multiplication (order 8; one irrep of quaternionic type).  Site 2u + s is the unit
+    u in (1, i, j, k) with sign (-1)^s."""
+    # unit products: UNIT[u][v] = (w, sign) with u v = sign * w
+    unit = [[(0, 1), (1, 1), (2, 1), (3, 1)],
+            [(1, 1), (0, -1), (3, 1), (2, -1)],
+            [(2, 1), (3, -1), (0, -1), (1, 1)],
+            [(3, 1), (2, 1), (1, -1), (0, -1)]]
+
+    def mul(x, y):
+        (u, su), (v, sv) = divmod(x, 2), divmod(y, 2)
+        w, sg = unit[u][v]
+        neg = (su + sv + (sg < 0)) % 2
+        return 2 * w + neg
+
+    gens = np.stack([np.array([mul(g, x) for x in range(8)], dtype=np.int32) for g in (2, 4)])
+    bonds = sorted({tuple(sorted((x, mul(x, c)))) for x in range(8) for c in (2, 4)})
+    return Cluster("q8", 8, np.array(bonds, dtype=np.int32), gens)
+
+
 def _dimer():
     return Cluster("dimer", 2, np.array([[0, 1]], dtype=np.int32), np.array([[1, 0]], dtype=np.int32))
 
@@ -166,8 +233,8 @@ def _square(lx, ly, pg):
 
 
 CLUSTER_NAMES = (
-    "dimer", "tetrahedron", "icosahedron", "dodecahedron", "icosidodecahedron", "cuboctahedron",
-    "ring:N", "square:LXxLY[:c4v|c2v|t]",
+    "dimer", "tetrahedron", "tetrahedron:t", "icosahedron", "dodecahedron", "icosidodecahedron", "cuboctahedron",
+    "ring:N", "chain:N", "square:LXxLY[:c4v|c2v|t]", "complete:P", "petersen", "q8",
 )
 
 
@@ -177,6 +244,16 @@ def cluster(name: str) -> Cluster:
         return _dimer()
     if name == "tetrahedron":
         return _tetrahedron()
+    if name == "tetrahedron:t":
+        return _tetrahedron_rotations()
+    if name == "petersen":
+        return _petersen()
+    if name == "q8":
+        return _q8()
+    if name.startswith("chain:"):
+        return _chain(int(name.split(":")[1]))
+    if name.startswith("complete:"):
+        return _complete(int(name.split(":")[1]))
     if name == "icosahedron":
         return _polyhedron(name, _icosahedron_vertices(), _ih_generators)
     if name == "dodecahedron":
