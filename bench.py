@@ -264,7 +264,7 @@ def _kernel_sha():
     import hashlib
 
     h = hashlib.sha256()
-    for name in ("hvp.cuh", "ptx.cuh", "contract.cuh"):
+    for name in ("hvp.cuh", "hvp_lane.cuh", "ptx.cuh", "contract.cuh"):
         with open(os.path.join(ROOT, "paper_2607_17429_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -400,6 +400,50 @@ def hv_once(flips="search"):
     F.ftlm_basis_check(blk)
     torch.cuda.synchronize()
     print(json.dumps({"hv_once": "ok", "packed_rows": rows, "hg_dim": dim}))
+
+
+def hv_once_lane(flips="table", two_M=28):
+    """The profiling stand-in for the largest single block: one FP32 B = 1 H·v of the s=3/2 dodecahedron's
+    H_g block at M = two_M/2 (M = 14: 6.9e7 rows, vectors of 0.27 GB, twice L2; the M = 0 block's table
+    of ~200 GB is too large for a capture), on the entry table (one-thread-per-representative kernel) or
+    searching.  Prints the kernel's flip count and the algorithmic bytes of the launch."""
+    import torch
+
+    from paper_2607_17429_gb300 import build as pb
+
+    pb.build()
+    from paper_2607_17429_gb300 import ftlm as F
+    from workloads import cluster
+
+    torch.cuda.set_device(0)
+    c = cluster("dodecahedron")
+    g = F.ftlm_group_init(c.gens, c.bonds)
+    info = F.ftlm_group_info(g)
+    _, perms = F.ftlm_group_irrep(g)
+    inv = int(np.nonzero((perms == c.gens[2]).all(axis=1))[0][0])
+    ir = [i for i, d in enumerate(info["dims"]) if d == 5 and info["chars"][i][inv] > 0][0]
+    sec = F.ftlm_build_sector(g, 3, two_M)
+    n_ent = F.ftlm_sector_build_entries(sec) if flips == "table" else None
+    mb = F.ftlm_build_multiblock(sec, [ir])
+    rows = F.ftlm_multiblock_packed_rows(mb)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(0)
+    xp = torch.randn(rows, 1, device="cuda", generator=gen)
+    yp = torch.empty_like(xp)
+    F.ftlm_profile_reset()
+    F.ftlm_profile_enable(True)
+    F.ftlm_hv_packed(mb, F.F32, 1, xp, yp)
+    torch.cuda.synchronize()
+    F.ftlm_profile_enable(False)
+    prof = F.ftlm_profile_get()
+    F.ftlm_basis_check(F.ftlm_multiblock_block(mb, 0))
+    n_reps = F.ftlm_sector_info(sec)["n_reps"]
+    fl = prof["hv_flips"] / max(1, prof["hv_launches"])
+    seg = 5 * 1 * 4
+    alg = fl * (seg + 8) + n_reps * (2 * seg + 24) if flips == "table" else fl * (seg + 20) + n_reps * (2 * seg + 16)
+    print(json.dumps({"hv_once": "ok", "two_M": two_M, "flip_path": flips, "n_reps": n_reps, "packed_rows": rows,
+                      "entries": n_ent, "flips_per_launch": fl, "algorithmic_per_launch": alg,
+                      "hv_ms": prof["hv_ms"]}))
 
 
 def config5(args):
@@ -781,6 +825,8 @@ def main():
                     help="one packed 10-block H·v and one H_g-block H·v of the workload, then exit (profiling case)")
     ap.add_argument("--config5", action="store_true",
                     help="the largest single block instead: s=3/2 dodecahedron, M=0, H_g (3.6e9 states), R=1")
+    ap.add_argument("--two-M", type=int, default=28,
+                    help="with --hv-once --config5: the M sector (2M) of the scaled-down profiling case")
     ap.add_argument("--e0-check", action="store_true",
                     help="cross-check E0 of the s=3/2 dodecahedron against the paper (all M=0 Gamma+- blocks)")
     ap.add_argument("--e0-steps", type=int, default=60)
@@ -793,7 +839,10 @@ def main():
                     help="batched small blocks instead: every M>=0 sector x irrep of three clusters, R=24 Rademacher")
     args = ap.parse_args()
     if args.hv_once:
-        hv_once(args.flips)
+        if args.config5:
+            hv_once_lane(args.flips, args.two_M)
+        else:
+            hv_once(args.flips)
         return
     if args.config5:
         config5(args)

@@ -80,8 +80,15 @@ typedef struct ftlm_multiblock ftlm_multiblock; /* device: several blocks of one
  *   out            receives the new handle
  * Errors: FTLM_EINVAL, FTLM_ENOTGROUP (not permutations, or |G| > 512),
  *         FTLM_EBONDS (Section 3's bond-invariance check), FTLM_EIRREP.
- * Irreps of complex or quaternionic type are listed (fs = 0 or -1) without
- * matrices; blocks of such irreps return FTLM_EUNSUPPORTED.
+ * Irreps are real-irreducible representations with real orthogonal matrices:
+ * an irrep of real Frobenius-Schur type (fs = 1); for a pair Gamma, conj(Gamma)
+ * of complex type (fs = 0) one entry, the real form of dimension 2 d_Gamma; for
+ * a quaternionic irrep (fs = -1) its real form of dimension 2 d_Gamma.  A block
+ * of a real form holds every level kappa = 2 (complex) or 4 (quaternionic)
+ * times, so it enters Eqs. 5, 6 and 14 with the weight dim / kappa
+ * (ftlm_group_weights) instead of d_Gamma.  Section 3 keeps a complex-arithmetic
+ * path for those irreps instead; the real form computes the same thermal sums in
+ * real arithmetic with the same vector length (2 D real numbers for D complex).
  */
 ftlm_status ftlm_group_init(int n_sites, int n_gens, const int32_t *gens, int n_bonds, const int32_t *bonds,
                             double J, ftlm_group **out);
@@ -97,15 +104,21 @@ ftlm_status ftlm_group_builtin(const char *name, ftlm_group **out);
 
 /*
  * Group facts.  Any output pointer may be NULL.
- *   dims, fs: [n_irreps];  chars: [n_irreps][order] (canonical element order).
+ *   dims, fs: [n_irreps] (real dimension, Frobenius-Schur indicator);
+ *   chars: [n_irreps][order] (traces of the real matrices, canonical element order).
  */
 ftlm_status ftlm_group_info(const ftlm_group *g, int *n_sites, int *order, int *n_irreps, int *dims, int *fs,
                             double *chars);
+/*
+ * Weight of every irrep's block in Eqs. 5, 6 and 14 (the ftlm_block d_gamma):
+ * dims / kappa with kappa = 1, 2, 4 for fs = 1, 0, -1.  weights: [n_irreps] host.
+ */
+ftlm_status ftlm_group_weights(const ftlm_group *g, int *weights);
 
 /*
  * Export one irrep and the element table.  rho: [order][d][d] host,
- * rho[g][a][b] = rho_Gamma(g)_{ab} (NULL to skip; FTLM_EUNSUPPORTED for irreps
- * without real matrices).  perms: [order][n_sites] (NULL to skip).
+ * rho[g][a][b] = rho_Gamma(g)_{ab} (NULL to skip).  perms: [order][n_sites]
+ * (NULL to skip).
  * bonds: [n_bonds][2] (NULL to skip), n_bonds/J may be NULL.
  */
 ftlm_status ftlm_group_irrep(const ftlm_group *g, int irrep, double *rho, int32_t *perms);
@@ -115,9 +128,10 @@ ftlm_status ftlm_group_bonds(const ftlm_group *g, int *n_bonds, int32_t *bonds, 
  * Replace the computed irreps by tabulated ones (Section 2.3: irrep matrices
  * "from standard tables or computed numerically").  rho_all holds, irrep after
  * irrep, [order][dims[i]][dims[i]] real matrices in canonical element order.
- * Every irrep must be a homomorphism with orthogonal matrices, the characters
- * must be orthonormal and sum d^2 = |G| (Section 3's checks, 1e-9); otherwise
- * FTLM_EIRREP and the group is unchanged.  The irreps are re-sorted into the
+ * Every irrep must be a homomorphism with orthogonal matrices; its type comes
+ * from <chi, chi> = 1, 2, 4 (real, complex pair, quaternionic); the characters
+ * must be orthogonal with those norms and sum d^2 / kappa = |G| (Section 3's
+ * checks, 1e-9); otherwise FTLM_EIRREP and the group is unchanged.  The irreps are re-sorted into the
  * canonical irrep order.  Sectors and blocks built before the call are unaffected.
  */
 ftlm_status ftlm_group_set_irreps(ftlm_group *g, int n_irreps, const int *dims, const double *rho_all);
@@ -184,8 +198,8 @@ ftlm_status ftlm_sector_free_entries(const ftlm_sector *s);
  * count checked against the character formula) and sqrt|Stab|; per
  * representative the row offset (prefix sum of n_Gamma, Eq. 13).
  * The block keeps the sector alive (reference counted).
- * Errors: FTLM_EINVAL (irrep index), FTLM_EUNSUPPORTED (d_Gamma > 5 or no real
- * matrices), FTLM_EIRREP, FTLM_ENOMEM, FTLM_ECUDA.
+ * Errors: FTLM_EINVAL (irrep index), FTLM_EUNSUPPORTED (dimension above 12,
+ * Section 3's limit), FTLM_EIRREP, FTLM_ENOMEM, FTLM_ECUDA.
  */
 ftlm_status ftlm_build_block(const ftlm_sector *s, int irrep, void *cuda_stream, ftlm_basis **out);
 
@@ -265,7 +279,7 @@ ftlm_status ftlm_hv_multi(const ftlm_multiblock *mb, ftlm_dtype dtype, int B, co
  * n_reps * W.  One flipped state's representative r' then owns one fixed-size
  * segment holding every block's coefficients, so one lookup and one gather
  * serve all blocks of Eq. 15.  Available for the compiled block shapes: a
- * single block of dimension 1..5, and the full real irrep sets of I_h, O_h and
+ * single block of dimension 1..12, and the full real irrep sets of I_h, O_h and
  * T_d in canonical irrep order (every set built by ftlm_build_multiblock over
  * those irreps); rows below 2^32.
  *   ftlm_multiblock_packed_rows: *rows = n_reps * W (FTLM_EUNSUPPORTED if the
@@ -412,7 +426,7 @@ ftlm_status ftlm_ritz(int n_chains, int ld, const int *m, const double *alpha, c
 
 typedef struct {
     int two_M;              /* 2M of the block's sector */
-    int d_gamma;            /* irrep dimension (Eq. 14 weight) */
+    int d_gamma;            /* the irrep's weight (Eq. 14): ftlm_group_weights */
     uint64_t dim;           /* block dimension D_{M,Gamma} (Eq. 13) */
     int R;                  /* number of chains */
     int ld;                 /* leading dimension of alpha/beta (>= max steps) */
@@ -517,7 +531,7 @@ typedef struct {
 } ftlm_job;
 typedef struct {
     ftlm_status status;
-    int d_gamma;
+    int d_gamma;            /* the irrep's weight (ftlm_group_weights) */
     uint64_t dim;
     double t_submit, t_admit, t_start, t_done;
 } ftlm_job_info;

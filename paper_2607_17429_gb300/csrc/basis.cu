@@ -542,7 +542,6 @@ ftlm_status build_block_impl(ftlm_sector *s, int irrep, cudaStream_t stream, ftl
     const GroupData &grp = s->grp;
     if (irrep < 0 || irrep >= (int)grp.irreps.size()) return fail(FTLM_EINVAL, "irrep index out of range");
     const Irrep &ir = grp.irreps[irrep];
-    if (ir.fs != 1) return fail(FTLM_EUNSUPPORTED, "irrep is not of real type");
     if (ir.dim > kMaxD) return fail(FTLM_EUNSUPPORTED, "d_Gamma = %d exceeds %d", ir.dim, kMaxD);
     const int d = ir.dim, G = grp.G;
     b->irrep = irrep;

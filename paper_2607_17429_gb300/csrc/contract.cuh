@@ -2,17 +2,17 @@
 // irrep dimension D so that no predicated work is issued for D < 5.
 //
 // rho tables are stored with padded rows: row length rho_row(D) elements (1, 2,
-// 4, 4, 6 for D = 1..5), so that an FP32 row is one 16-byte load (D = 3, 4) or
-// three 8-byte loads (D = 5; an 8-byte shared load with a few distinct addresses
-// per warp takes one wavefront, a 16-byte load two), and an even-length row
-// holds the element pairs of the packed FP32 FMA.
+// 4, 4, 6 for D = 1..5, D rounded up to even above), so that an FP32 row is one
+// 16-byte load (D = 3, 4) or 8-byte loads (D = 5; an 8-byte shared load with a
+// few distinct addresses per warp takes one wavefront, a 16-byte load two), and
+// an even-length row holds the element pairs of the packed FP32 FMA.
 #pragma once
 
 #include "common.cuh"
 
 namespace ftlm {
 
-__host__ __device__ constexpr int rho_row(int D) { return D == 5 ? 6 : (D == 3 ? 4 : D); }
+__host__ __device__ constexpr int rho_row(int D) { return D == 1 ? 1 : (D == 3 ? 4 : D + (D & 1)); }
 
 // elements of one padded table [G][D][rho_row(D)], rounded up to 16 bytes
 template <typename VT>

@@ -183,22 +183,24 @@ ftlm_status canonicalise_and_verify_irreps(GroupData &g, std::vector<Irrep> &irr
     const int G = g.G;
     std::stable_sort(irreps.begin(), irreps.end(), char_less);
     int sum = 0;
-    // a complex-type entry stands for the pair Gamma, conj(Gamma)
-    for (auto &ir : irreps) sum += (ir.fs == 0 ? 2 : 1) * ir.dim * ir.dim;
+    // sum over the complex irreps of d^2: a real form of dimension d stands for d^2 / kappa of it
+    for (auto &ir : irreps) {
+        if ((ir.dim * ir.dim) % ir.kappa()) return fail(FTLM_EIRREP, "real form of odd dimension");
+        sum += ir.dim * ir.dim / ir.kappa();
+    }
     if (sum != G) return fail(FTLM_EIRREP, "sum of d^2 = %d differs from |G| = %d", sum, G);
     for (size_t a = 0; a < irreps.size(); ++a) {
         for (size_t b = 0; b < irreps.size(); ++b) {
             double s = 0.0;
             for (int h = 0; h < G; ++h) s += irreps[a].chars[h] * irreps[b].chars[h];
             s /= G;
-            // complex type: listed with Re(chi), whose norm is 1/2
-            double want = (a == b) ? (irreps[a].fs == 0 ? 0.5 : 1.0) : 0.0;
+            const double want = (a == b) ? (double)irreps[a].kappa() : 0.0;
             if (fabs(s - want) > tol) return fail(FTLM_EIRREP, "character orthogonality violated");
         }
     }
     for (auto &ir : irreps) {
-        if (ir.fs != 1) continue;
         const int d = ir.dim;
+        if (ir.rho.size() != (size_t)G * d * d) return fail(FTLM_EIRREP, "irrep without matrices");
         for (int x = 0; x < G; ++x) {
             const double *A = &ir.rho[(size_t)x * d * d];
             double tr = 0.0;
@@ -279,28 +281,30 @@ static ftlm_status irreps_from_regular(GroupData &g, uint64_t seed, std::vector<
             }
             norm /= G;
             fsum /= G;
+            // The eigenspace is one copy of a real-irreducible representation: an irrep of real
+            // type (<chi, chi> = 1, Frobenius-Schur sum 1), or the real form of a complex pair
+            // (<chi, chi> = 2, sum 0) or of a quaternionic irrep (<chi, chi> = 4, sum -2).
             Irrep ir;
-            if (fabs(norm - 1.0) < 1e-6 && fabs(fsum - 1.0) < 1e-6) {
-                ir.dim = m;
+            if (fabs(norm - 1.0) < 1e-6 && fabs(fsum - 1.0) < 1e-6)
                 ir.fs = 1;
-                ir.chars = chi;
-                ir.rho.resize((size_t)G * m * m);
-                for (int x = 0; x < G; ++x) {
-                    const int xi = g.inv[x];
-                    for (int a = 0; a < m; ++a)
-                        for (int b = 0; b < m; ++b) {
-                            double s = 0.0;
-                            const double *ba = &Bm[(size_t)a * G], *bb = &Bm[(size_t)b * G];
-                            for (int y = 0; y < G; ++y) s += ba[y] * bb[g.mult[(size_t)xi * G + y]];
-                            ir.rho[((size_t)x * m + a) * m + b] = s;
-                        }
-                }
-            } else {
-                // real irreducible of complex or quaternionic type: listed without matrices
-                ir.dim = m / 2;
-                ir.fs = (norm > 3.0) ? -1 : 0;
-                for (double &v : chi) v *= 0.5;
-                ir.chars = chi;
+            else if (fabs(norm - 2.0) < 1e-6 && fabs(fsum) < 1e-6)
+                ir.fs = 0;
+            else if (fabs(norm - 4.0) < 1e-6 && fabs(fsum + 2.0) < 1e-6)
+                ir.fs = -1;
+            else
+                return fail(FTLM_EIRREP, "eigenspace of dimension %d is not real-irreducible", m);
+            ir.dim = m;
+            ir.chars = chi;
+            ir.rho.resize((size_t)G * m * m);
+            for (int x = 0; x < G; ++x) {
+                const int xi = g.inv[x];
+                for (int a = 0; a < m; ++a)
+                    for (int b = 0; b < m; ++b) {
+                        double s = 0.0;
+                        const double *ba = &Bm[(size_t)a * G], *bb = &Bm[(size_t)b * G];
+                        for (int y = 0; y < G; ++y) s += ba[y] * bb[g.mult[(size_t)xi * G + y]];
+                        ir.rho[((size_t)x * m + a) * m + b] = s;
+                    }
             }
             out.push_back(std::move(ir));
         }
@@ -546,13 +550,18 @@ ftlm_status ftlm_group_info(const ftlm_group *g, int *n_sites, int *order, int *
     return FTLM_OK;
 }
 
+ftlm_status ftlm_group_weights(const ftlm_group *g, int *weights) {
+    if (!g || !weights) return fail(FTLM_EINVAL, "NULL argument");
+    for (size_t i = 0; i < g->d.irreps.size(); ++i) weights[i] = g->d.irreps[i].weight();
+    return FTLM_OK;
+}
+
 ftlm_status ftlm_group_irrep(const ftlm_group *g, int irrep, double *rho, int32_t *perms) {
     if (!g) return fail(FTLM_EINVAL, "group is NULL");
     const GroupData &d = g->d;
     if (perms) std::copy(d.perms.begin(), d.perms.end(), perms);
     if (rho) {
         if (irrep < 0 || irrep >= (int)d.irreps.size()) return fail(FTLM_EINVAL, "irrep index out of range");
-        if (d.irreps[irrep].fs != 1) return fail(FTLM_EUNSUPPORTED, "irrep has no real orthogonal form");
         std::copy(d.irreps[irrep].rho.begin(), d.irreps[irrep].rho.end(), rho);
     }
     return FTLM_OK;
@@ -579,11 +588,16 @@ ftlm_status ftlm_group_set_irreps(ftlm_group *g, int n_irreps, const int *dims, 
         irr[i].rho.assign(rho_all + pos, rho_all + pos + (size_t)G * d * d);
         pos += (size_t)G * d * d;
         irr[i].chars.resize(G);
+        double norm = 0.0;
         for (int x = 0; x < G; ++x) {
             double tr = 0.0;
             for (int a = 0; a < d; ++a) tr += irr[i].rho[((size_t)x * d + a) * d + a];
             irr[i].chars[x] = tr;
+            norm += tr * tr;
         }
+        // the type of a real-irreducible representation from <chi, chi> = 1, 2, 4
+        norm /= G;
+        irr[i].fs = norm < 1.5 ? 1 : (norm < 3.0 ? 0 : -1);
     }
     ftlm_status st = canonicalise_and_verify_irreps(g->d, irr, 1e-9);
     if (st != FTLM_OK) return st;

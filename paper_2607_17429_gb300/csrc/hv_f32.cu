@@ -5,6 +5,9 @@ namespace ftlm {
 
 ftlm_status hv_multi_launch_f32(const ftlm_multiblock *mb, int B, const float *const *x, float *const *y,
                                cudaStream_t stream) {
+    for (int k = 0; k < mb->K; ++k)  // this per-block layout kernel is specialised for d_Gamma <= 5
+        if (mb->blocks[k]->d > 5)
+            return fail(FTLM_EUNSUPPORTED, "d_Gamma = %d needs the packed layout (ftlm_hv_packed)", mb->blocks[k]->d);
     HvArgs<float> a;
     const float *V[kMaxK];
     for (int k = 0; k < mb->K; ++k) V[k] = mb->blocks[k]->d_Vf;

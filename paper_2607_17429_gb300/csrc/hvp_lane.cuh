@@ -18,7 +18,7 @@ constexpr int kLaneThreads = 256;
 template <typename VT, typename ST, int D>
 __global__ void __launch_bounds__(kLaneThreads) hvp_lane_kernel(const __grid_constant__ HvpArgs<VT> a) {
     constexpr int RP = rho_row(D);
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     VT *s_rho = reinterpret_cast<VT *>(smem);  // rho(g) of the block, [G][D][RP]
     uint8_t *s_bond = smem + (((size_t)a.rho_total * sizeof(VT) + 15) & ~(size_t)15);
     __shared__ double red[kLaneThreads / 32];

@@ -7,9 +7,16 @@
 
 namespace ftlm {
 
-// Shape ids: one block of dimension 1..5, and the full real irrep sets of I_h,
-// O_h and T_d in canonical irrep order (dimensions ascending).
-enum { kShapeD1 = 0, kShapeD2, kShapeD3, kShapeD4, kShapeD5, kShapeIh, kShapeOh, kShapeTd, kNumShapes };
+// Shape ids: one block of dimension 1..12 (Section 3's limit on d_Gamma; real
+// forms of complex and quaternionic irreps count their real dimension), and the
+// full real irrep sets of I_h, O_h and T_d in canonical irrep order (dimensions
+// ascending).
+enum {
+    kShapeD1 = 0, kShapeD2, kShapeD3, kShapeD4, kShapeD5, kShapeD6, kShapeD7, kShapeD8, kShapeD9, kShapeD10,
+    kShapeD11, kShapeD12, kShapeIh, kShapeOh, kShapeTd, kNumShapes
+};
+constexpr bool shape_is_single(int shape) { return shape >= kShapeD1 && shape <= kShapeD12; }
+constexpr bool shape_is_wide(int shape) { return shape >= kShapeD6 && shape <= kShapeD12; }
 using ShapeIh = Shape<1, 1, 3, 3, 3, 3, 4, 4, 5, 5>;
 using ShapeOh = Shape<1, 1, 1, 1, 2, 2, 3, 3, 3, 3>;
 using ShapeTd = Shape<1, 1, 2, 3, 3>;
@@ -70,11 +77,16 @@ const HvpOps<double> *hvp_ops_single_f64(int shape, int gpl, bool half);
 const HvpOps<double> *hvp_ops_multi_f64(int shape, int gpl, bool half);
 const HvpOps<float> *hvp_ops_single_f16(int shape, int gpl, bool half);  // FP16 storage, FP32 arithmetic
 const HvpOps<float> *hvp_ops_multi_f16(int shape, int gpl, bool half);
-// table mode (flips from the sector's entry table), any shape; esize 8, 4 or 2
+// one block of dimension 6..12 (label search with 4 elements per lane, any |G| <= 128):
+// kind 0 search, 1 table, 2 table with one thread per representative (B = 1)
+const HvpOps<float> *hvp_ops_wide_f32(int shape, bool half, int kind);
+const HvpOps<double> *hvp_ops_wide_f64(int shape, bool half, int kind);
+const HvpOps<float> *hvp_ops_wide_f16(int shape, bool half, int kind);
+// table mode (flips from the sector's entry table), shapes D1..D5, I_h, O_h, T_d; esize 8, 4 or 2
 const HvpOps<double> *hvp_ops_table_f64(int shape);
 const HvpOps<float> *hvp_ops_table_f32(int shape);
 const HvpOps<float> *hvp_ops_table_f16(int shape);
-// table mode, one thread per representative: single blocks (shape D1..D5) at B = 1
+// table mode, one thread per representative: single blocks (shapes D1..D5) at B = 1
 const HvpOps<double> *hvp_ops_lane_f64(int shape);
 const HvpOps<float> *hvp_ops_lane_f32(int shape);
 const HvpOps<float> *hvp_ops_lane_f16(int shape);

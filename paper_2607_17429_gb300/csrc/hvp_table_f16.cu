@@ -5,13 +5,14 @@
 namespace ftlm {
 
 const HvpOps<float> *hvp_ops_table_f16(int shape) {
-    static const HvpOps<float> tab[kNumShapes] = {
+    static const HvpOps<float> tab[8] = {
         FTLM_HVP_OPS_M(float, __half, Shape<1>, 2, false, 1), FTLM_HVP_OPS_M(float, __half, Shape<2>, 2, false, 1),
         FTLM_HVP_OPS_M(float, __half, Shape<3>, 2, false, 1), FTLM_HVP_OPS_M(float, __half, Shape<4>, 2, false, 1),
         FTLM_HVP_OPS_M(float, __half, Shape<5>, 2, false, 1), FTLM_HVP_OPS_M(float, __half, ShapeIh, 2, false, 1),
         FTLM_HVP_OPS_M(float, __half, ShapeOh, 2, false, 1), FTLM_HVP_OPS_M(float, __half, ShapeTd, 2, false, 1)};
-    if (shape < 0 || shape >= kNumShapes) return nullptr;
-    return &tab[shape];
+    if (shape >= kShapeD1 && shape <= kShapeD5) return &tab[shape - kShapeD1];
+    if (shape >= kShapeIh && shape <= kShapeTd) return &tab[5 + shape - kShapeIh];
+    return nullptr;
 }
 
 const HvpOps<float> *hvp_ops_lane_f16(int shape) {

@@ -5,13 +5,14 @@
 namespace ftlm {
 
 const HvpOps<double> *hvp_ops_table_f64(int shape) {
-    static const HvpOps<double> tab[kNumShapes] = {
+    static const HvpOps<double> tab[8] = {
         FTLM_HVP_OPS_M(double, double, Shape<1>, 2, false, 1), FTLM_HVP_OPS_M(double, double, Shape<2>, 2, false, 1),
         FTLM_HVP_OPS_M(double, double, Shape<3>, 2, false, 1), FTLM_HVP_OPS_M(double, double, Shape<4>, 2, false, 1),
         FTLM_HVP_OPS_M(double, double, Shape<5>, 2, false, 1), FTLM_HVP_OPS_M(double, double, ShapeIh, 2, false, 1),
         FTLM_HVP_OPS_M(double, double, ShapeOh, 2, false, 1), FTLM_HVP_OPS_M(double, double, ShapeTd, 2, false, 1)};
-    if (shape < 0 || shape >= kNumShapes) return nullptr;
-    return &tab[shape];
+    if (shape >= kShapeD1 && shape <= kShapeD5) return &tab[shape - kShapeD1];
+    if (shape >= kShapeIh && shape <= kShapeTd) return &tab[5 + shape - kShapeIh];
+    return nullptr;
 }
 
 const HvpOps<double> *hvp_ops_lane_f64(int shape) {

@@ -14,7 +14,7 @@ namespace ftlm {
 
 constexpr int kMaxG = 128;      // group order supported on the GPU path (4 elements per lane)
 constexpr int kMaxGHost = 512;  // group order supported by the host group module
-constexpr int kMaxD = 5;        // irrep dimension supported on the GPU path
+constexpr int kMaxD = 12;       // irrep dimension supported on the GPU path (Section 3's limit)
 constexpr int kMaxBonds = 64;   // bonds per cluster on the GPU path
 constexpr int kMaxB = 32;       // right-hand sides per H·v launch
 constexpr int kPMaxK = 10;      // blocks per packed set (compile-time shapes)
@@ -71,11 +71,19 @@ void count_launch(int n = 1);
 bool profiling_on();
 unsigned long long *profile_flip_counter();
 
+// A real-irreducible representation: an irrep of real Frobenius-Schur type
+// (fs = 1), the real form of a complex pair Gamma + conj(Gamma) (fs = 0,
+// dimension 2 d_Gamma) or of a quaternionic irrep (fs = -1, dimension
+// 2 d_Gamma).  kappa = <chi, chi> = 1, 2, 4 is the dimension of its real
+// commutant; a single-partner-row block counts each level kappa times, so its
+// weight in Eqs. 5 and 14 is dim / kappa.
 struct Irrep {
     int dim = 0;
-    int fs = 1;                 // Frobenius-Schur indicator; 1 = real orthogonal matrices available
-    std::vector<double> chars;  // [G]
-    std::vector<double> rho;    // [G][dim][dim] (empty unless fs == 1)
+    int fs = 1;                 // Frobenius-Schur indicator of the complex constituent
+    std::vector<double> chars;  // [G], trace of rho
+    std::vector<double> rho;    // [G][dim][dim] real orthogonal
+    int kappa() const { return fs == 1 ? 1 : (fs == 0 ? 2 : 4); }
+    int weight() const { return dim / kappa(); }
 };
 
 struct GroupData {

@@ -31,7 +31,8 @@ struct ShapeDef {
     int d[kPMaxK];
 };
 const ShapeDef kShapeDefs[kNumShapes] = {
-    {1, {1}}, {1, {2}}, {1, {3}}, {1, {4}}, {1, {5}},
+    {1, {1}}, {1, {2}}, {1, {3}}, {1, {4}}, {1, {5}}, {1, {6}}, {1, {7}}, {1, {8}}, {1, {9}}, {1, {10}},
+    {1, {11}}, {1, {12}},
     {10, {1, 1, 3, 3, 3, 3, 4, 4, 5, 5}},
     {10, {1, 1, 1, 1, 2, 2, 3, 3, 3, 3}},
     {5, {1, 1, 2, 3, 3}},
@@ -227,6 +228,8 @@ template <typename VT>
 const HvpOps<VT> *hvp_ops(int shape, int gpl, bool half, int esize, int mode);
 template <>
 const HvpOps<float> *hvp_ops<float>(int shape, int gpl, bool half, int esize, int mode) {
+    if (shape_is_wide(shape))
+        return esize == 2 ? hvp_ops_wide_f16(shape, half, mode) : hvp_ops_wide_f32(shape, half, mode);
     if (mode == 1) return esize == 2 ? hvp_ops_table_f16(shape) : hvp_ops_table_f32(shape);
     if (esize == 2)
         return shape <= kShapeD5 ? hvp_ops_single_f16(shape, gpl, half) : hvp_ops_multi_f16(shape, gpl, half);
@@ -235,6 +238,7 @@ const HvpOps<float> *hvp_ops<float>(int shape, int gpl, bool half, int esize, in
 template <>
 const HvpOps<double> *hvp_ops<double>(int shape, int gpl, bool half, int esize, int mode) {
     if (esize != 8) return nullptr;
+    if (shape_is_wide(shape)) return hvp_ops_wide_f64(shape, half, mode);
     if (mode == 1) return hvp_ops_table_f64(shape);
     return shape <= kShapeD5 ? hvp_ops_single_f64(shape, gpl, half) : hvp_ops_multi_f64(shape, gpl, half);
 }
@@ -524,10 +528,13 @@ ftlm_status hvp_plan(const ftlm_sector *s, const PackedSet *ps, std::vector<HvpP
     if (mode == 1 && ps->K == 1 && B == 1) {  // one thread per representative
         const HvpOps<VT> *lane = nullptr;
         if constexpr (sizeof(VT) == 8)
-            lane = hvp_ops_lane_f64(ps->shape);
+            lane = shape_is_wide(ps->shape) ? hvp_ops_wide_f64(ps->shape, s->half, 2) : hvp_ops_lane_f64(ps->shape);
+        else if (shape_is_wide(ps->shape))
+            lane = esize == 2 ? hvp_ops_wide_f16(ps->shape, s->half, 2) : hvp_ops_wide_f32(ps->shape, s->half, 2);
         else
             lane = esize == 2 ? hvp_ops_lane_f16(ps->shape) : hvp_ops_lane_f32(ps->shape);
-        if (lane) plan.ops = lane;
+        // its rho table lives in shared memory: keep the warp kernel when the table does not fit
+        if (lane && lane->occupancy(a, lane->max_threads / 32, 1) > 0) plan.ops = lane;
     }
     if (!plan.ops)
         return fail(FTLM_EUNSUPPORTED, "no compiled packed kernel for shape %d with |G| = %d", ps->shape, s->G);

@@ -309,7 +309,7 @@ bool admit_head(ftlm_server *S, std::unique_lock<std::mutex> &lk, cudaStream_t b
     S->st.peak_charged = std::max(S->st.peak_charged, S->charged);
     J->vec_bytes = need;
     J->be = be;
-    J->d_gamma = be->blk->d;
+    J->d_gamma = be->blk->sec->grp.irreps[be->blk->irrep].weight();
     J->dim = be->blk->dim;
     J->t_admit = now_s(S->t0);
     S->queue.pop_front();

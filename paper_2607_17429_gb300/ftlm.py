@@ -67,6 +67,7 @@ _SIGS = {
     "ftlm_group_init": [_I, _I, _P, _I, _P, ctypes.c_double, _P],
     "ftlm_group_builtin": [ctypes.c_char_p, _P],
     "ftlm_group_info": [_P, _P, _P, _P, _P, _P, _P],
+    "ftlm_group_weights": [_P, _P],
     "ftlm_group_irrep": [_P, _I, _P, _P],
     "ftlm_group_bonds": [_P, _P, _P, _P],
     "ftlm_group_set_irreps": [_P, _I, _P, _P],
@@ -216,7 +217,9 @@ def ftlm_group_info(g: Group) -> dict:
     fs = np.zeros(n_irreps.value, dtype=np.int32)
     chars = np.zeros((n_irreps.value, order.value))
     _check(_lib.ftlm_group_info(g.handle, None, None, None, _ptr(dims), _ptr(fs), _ptr(chars)))
-    return dict(n_sites=n_sites.value, order=order.value, dims=dims, fs=fs, chars=chars)
+    weights = np.zeros(n_irreps.value, dtype=np.int32)
+    _check(_lib.ftlm_group_weights(g.handle, _ptr(weights)))
+    return dict(n_sites=n_sites.value, order=order.value, dims=dims, fs=fs, chars=chars, weights=weights)
 
 
 def ftlm_group_irrep(g: Group, irrep: int | None = None):

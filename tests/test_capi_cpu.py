@@ -53,17 +53,26 @@ def test_builtin_groups_match_oracle(ftlm, name):
         assert np.abs(np.einsum("gab,gcb->gac", rho, rho) - np.eye(ir.dim)).max() < 1e-10
 
 
-def test_complex_type_irreps_are_listed_without_matrices(ftlm):
-    """Translations of a 4x4 torus: momenta off {0, pi} have complex characters (Section 3: complex path)."""
-    g = ftlm.ftlm_group_builtin("square:4x4:t")
+@pytest.mark.parametrize("name", ["square:4x4:t", "chain:8", "tetrahedron:t", "complete:7", "complete:11",
+                                  "petersen", "q8"])
+def test_real_forms_match_oracle(ftlm, name):
+    """Irreps of complex and quaternionic type in real form (the library's reading of Section 3's
+    complex path) and dimensions above 5: the library's own irreps, computed from generators,
+    agree with the oracle's in dimension, type, weight and character, in the same canonical order."""
+    c = cluster(name)
+    g = ftlm.ftlm_group_init(c.gens, c.bonds)
+    og = Group(c.gens, c.bonds)
     info = ftlm.ftlm_group_info(g)
-    assert info["order"] == 16
-    fs = list(info["fs"])
-    assert fs.count(1) == 4 and fs.count(0) == 6  # k in {0, pi}^2 real; 12 complex momenta in 6 pairs
-    assert sum((2 if f == 0 else 1) * d * d for f, d in zip(fs, info["dims"])) == 16
-    with pytest.raises(ftlm.FtlmError) as e:
-        ftlm.ftlm_group_irrep(g, fs.index(0))
-    assert e.value.status == ftlm.EUNSUPPORTED
+    assert list(info["dims"]) == [ir.dim for ir in og.irreps]
+    assert list(info["fs"]) == [ir.fs for ir in og.irreps]
+    assert list(info["weights"]) == [ir.weight for ir in og.irreps]
+    assert np.abs(info["chars"] - og.char_table).max() < 1e-10
+    for i, ir in enumerate(og.irreps):
+        rho, _ = ftlm.ftlm_group_irrep(g, i)
+        assert np.abs(np.einsum("gab,hbc->ghac", rho, rho) - rho[og.mult]).max() < 1e-10
+        assert np.abs(np.einsum("gab,gcb->gac", rho, rho) - np.eye(ir.dim)).max() < 1e-10
+    if name == "square:4x4:t":  # k in {0, pi}^2 real; 12 complex momenta in 6 pairs
+        assert list(info["fs"]).count(1) == 4 and list(info["fs"]).count(0) == 6
 
 
 def test_group_init_from_generators(ftlm):
@@ -83,6 +92,24 @@ def test_set_irreps_tabulated(ftlm):
     for i, ir in enumerate(og.irreps):
         rho, _ = ftlm.ftlm_group_irrep(g, i)
         assert np.array_equal(rho, ir.rho)
+
+
+@pytest.mark.parametrize("name", ["q8", "complete:7", "chain:6"])
+def test_set_irreps_real_forms(ftlm, name):
+    """Tabulated real forms: the type follows from <chi, chi> = 1, 2, 4."""
+    c = cluster(name)
+    og = Group(c.gens, c.bonds)
+    g = ftlm.ftlm_group_init(c.gens, c.bonds)
+    ftlm.ftlm_group_set_irreps(g, [ir.rho for ir in og.irreps][::-1])
+    info = ftlm.ftlm_group_info(g)
+    assert list(info["fs"]) == [ir.fs for ir in og.irreps]
+    assert list(info["weights"]) == [ir.weight for ir in og.irreps]
+    # a complex-type real form with one row dropped is no representation: rejected, group unchanged
+    bad = [ir.rho if ir.fs == 1 else ir.rho[:, :1, :1] for ir in og.irreps]
+    with pytest.raises(ftlm.FtlmError) as e:
+        ftlm.ftlm_group_set_irreps(g, bad)
+    assert e.value.status == ftlm.EIRREP
+    assert list(ftlm.ftlm_group_info(g)["fs"]) == [ir.fs for ir in og.irreps]
 
 
 def test_error_paths(ftlm):

@@ -90,7 +90,9 @@ def test_dodecahedron_s32_m0_hg_full_size():
     # the entry table (2.5e10 flips x 8 bytes) reproduces the search path on the whole packed vector
     # (FP16 storage keeps the two vectors and the table within the device: about 275 GB at the peak);
     # at B = 1 the table path runs one thread per representative and sums the flips in entry order,
-    # so the FP32 sums differ in rounding and the FP16 outputs by at most one FP16 rounding step
+    # so the FP32 sums differ in rounding; where a row's terms cancel, that difference can exceed
+    # one FP16 step of the row's own value, so the bound is normwise, 2e-3 of the largest output
+    # (two FP16 steps there), as for the one-thread kernel on the small cases
     del blk
     torch.cuda.empty_cache()
     mb = F.ftlm_build_multiblock(sec, [ir])
@@ -108,9 +110,12 @@ def test_dodecahedron_s32_m0_hg_full_size():
     F.ftlm_basis_check(F.ftlm_multiblock_block(mb, 0))
     F.ftlm_sector_free_entries(sec)
     del x
+    ymax, dmax = 0.0, 0.0
     for c0 in range(0, rows, 1 << 28):  # compared in chunks: FP32 copies of the whole vectors do not fit
         ys = y_search[c0:c0 + (1 << 28)].float()
         yt = y_table[c0:c0 + (1 << 28)].float()
-        assert bool(((ys - yt).abs() <= 2.0 ** -10 * ys.abs() + 1e-6).all())
+        ymax = max(ymax, float(ys.abs().max()))
+        dmax = max(dmax, float((ys - yt).abs().max()))
+    assert dmax <= 2e-3 * (ymax + 1.0), (dmax, ymax)
     del y_search, y_table, ys, yt
     torch.cuda.empty_cache()
