@@ -583,7 +583,9 @@ ftlm_status ftlm_profile_get(ftlm_profile *out);
  *   FTLM_PEAK_GATHER                      bytes per second of random aligned segments
  *                                         of seg bytes (a multiple of 16) read from a
  *                                         device buffer of span bytes (the segments
- *                                         drawn from the first 2^floor(log2(span/seg)))
+ *                                         drawn from the first 2^floor(log2(span/seg)));
+ *                                         segments of at most 64 bytes one per lane,
+ *                                         longer ones one per warp
  *   FTLM_PEAK_STREAM                      bytes per second (read + write) of a copy
  *                                         of span bytes
  * span and seg are ignored by the arithmetic probes.  The gather and stream

@@ -132,6 +132,32 @@ __global__ void gather_probe(const uint4 *buf, uint64_t seg_mask, int seg_u4, in
     if (acc == 0x13572468u) sink[0] = acc;
 }
 
+// Segments of at most 64 bytes: every lane gathers its own segments (four in flight), as the
+// one-thread-per-representative H·v does with its 8..60-byte rows.
+__global__ void gather_lane_probe(const uint4 *buf, uint64_t seg_mask, int seg_u4, int per_lane, uint32_t *sink) {
+    const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+    for (int it = 0; it < per_lane; it += 4) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t s = mix64(t * 0x100000001ull + (uint64_t)(it + u)) & seg_mask;
+            const uint4 *p = buf + s * (uint64_t)seg_u4;
+            v[u] = __ldcg(p);
+            for (int q = 1; q < seg_u4; ++q) {
+                const uint4 w = __ldcg(p + q);
+                v[u].x ^= w.x;
+                v[u].y ^= w.y;
+                v[u].z ^= w.z;
+                v[u].w ^= w.w;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc ^= v[u].x ^ v[u].y ^ v[u].z ^ v[u].w;
+    }
+    if (acc == 0x13572468u) sink[0] = acc;
+}
+
 __global__ void copy_probe(const uint4 *src, uint4 *dst, uint64_t n) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
         dst[i] = __ldcs(src + i);
@@ -221,6 +247,17 @@ extern "C" ftlm_status ftlm_peak_probe(int kind, uint64_t span, int seg, void *c
             FTLM_CUDA(cudaMemsetAsync(buf.p, 0x5a, span / 16 * 16, st));
             uint64_t n_seg = 1;
             while (2 * n_seg <= span / (uint64_t)seg) n_seg *= 2;
+            if (seg <= 64) {  // one segment per lane: about 1 GB of segments per timed launch
+                const uint64_t lanes_all = (uint64_t)grid * kProbeThreads;
+                int per_lane = (int)std::min<uint64_t>(1 << 12, ((1ull << 30) / (uint64_t)seg + lanes_all - 1) / lanes_all);
+                per_lane = (per_lane + 3) & ~3;
+                auto go = [&] {
+                    gather_lane_probe<<<grid, kProbeThreads, 0, st>>>(buf.p, n_seg - 1, seg / 16, per_lane, sink.p);
+                };
+                if ((s = time_it(go, st, &ms)) != FTLM_OK) return s;
+                *rate = (double)lanes_all * per_lane * seg / (ms * 1e-3);
+                break;
+            }
             const int warps = grid * kProbeThreads / 32;
             // about 4 GB of segments per timed launch
             int per_warp = (int)std::min<uint64_t>(1 << 16, ((4ull << 30) / (uint64_t)seg + warps - 1) / warps);
