@@ -491,7 +491,7 @@ ftlm_status ftlm_thermo_noalloc(int n_chains, int ld, const int *m, const double
  *
  * A job is one block (2M, irrep) of a group's cluster at spin 2s with R
  * chains (1..32) of n_steps (1..512) Lanczos steps, its own block_id (Philox
- * key word 1, Section 2.2 reading C9) and the seed, generator and dtype of
+ * key word 1 of the start vectors) and the seed, generator and dtype of
  * ftlm_lanczos.  The server owns a scheduler thread and n_workers worker
  * threads, each with its own CUDA stream on the device current at creation.
  *  - Admission: jobs are admitted in submission order while the device bytes

@@ -15,6 +15,63 @@ namespace ftlm {
 
 constexpr int kLaneThreads = 256;
 
+__host__ __device__ constexpr int lane_gcd(int a, int b) { return b == 0 ? a : lane_gcd(b, a % b); }
+
+// Element j of a span of 32-bit words (j a compile-time constant after unrolling).
+template <typename ST>
+__device__ __forceinline__ ST span_elem(const uint32_t *w, int j) {
+    if constexpr (sizeof(ST) == 2) {
+        return __ushort_as_half((unsigned short)(w[j >> 1] >> (16 * (j & 1))));
+    } else if constexpr (sizeof(ST) == 4) {
+        return __uint_as_float(w[j]);
+    } else {
+        return __hiloint2double((int)w[2 * j + 1], (int)w[2 * j]);
+    }
+}
+
+// The D stored elements of row r of x (D * sizeof(ST) bytes from byte r * D * sizeof(ST)).  A row
+// starts at a multiple of gcd(D * sizeof(ST), 16) bytes past a 16-byte boundary, so the L aligned
+// 16-byte words from that boundary cover it: L vector loads per lane instead of D scalar ones, a
+// warp's gather then takes about 32 L sector lookups in L1 instead of 32 D.  The row is picked
+// out of the words by its offset (selects over the possible offsets, no local memory).  Rows
+// whose covering words would pass the end of x (n_elems elements), or an x that is not 16-byte
+// aligned, take scalar loads.
+template <typename VT, typename ST, int D>
+__device__ __forceinline__ void lane_row(const ST *__restrict__ x, uint64_t r, uint64_t n_elems, bool vec,
+                                         VT (&u)[D]) {
+    constexpr int E = (int)sizeof(ST), RB = D * E, PER = 16 / E;
+    constexpr int G = lane_gcd(RB, 16);
+    constexpr int L = (16 - G + RB + 15) / 16;  // words covering a row at the largest offset
+    constexpr int STEP = G / E, NOFF = 16 / G;  // offsets 0, STEP, ..., (NOFF - 1) STEP elements
+    const uint64_t e0 = r * D, w0 = e0 / PER;
+    if (vec && (w0 + L) * PER <= n_elems) {
+        uint32_t w[4 * L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(x) + w0 + l);
+            w[4 * l] = v.x;
+            w[4 * l + 1] = v.y;
+            w[4 * l + 2] = v.z;
+            w[4 * l + 3] = v.w;
+        }
+        const int off = (int)(e0 - w0 * PER);
+#pragma unroll
+        for (int g = 0; g < D; ++g) u[g] = st_get<VT, ST>(span_elem<ST>(w, g));
+#pragma unroll
+        for (int k = 1; k < NOFF; ++k) {
+            const bool hit = off == k * STEP;
+#pragma unroll
+            for (int g = 0; g < D; ++g) {
+                const VT v = st_get<VT, ST>(span_elem<ST>(w, k * STEP + g));
+                u[g] = hit ? v : u[g];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int g = 0; g < D; ++g) u[g] = st_get<VT, ST>(__ldg(x + e0 + g));
+    }
+}
+
 template <typename VT, typename ST, int D>
 __global__ void __launch_bounds__(kLaneThreads) hvp_lane_kernel(const __grid_constant__ HvpArgs<VT> a) {
     constexpr int RP = rho_row(D);
@@ -67,6 +124,8 @@ __global__ void __launch_bounds__(kLaneThreads) hvp_lane_kernel(const __grid_con
         if (rep >= P.n_reps) continue;
         const ST *__restrict__ x = static_cast<const ST *>(P.x);
         ST *__restrict__ y = static_cast<ST *>(P.y);
+        const uint64_t n_elems = P.n_reps * (uint64_t)D;
+        const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
         const HvRec rr = P.rec[rep];
         const int sid = (int)rr.sid;
         const size_t seg = rr.off;  // W = D rows, B = 1
@@ -99,8 +158,7 @@ __global__ void __launch_bounds__(kLaneThreads) hvp_lane_kernel(const __grid_con
             VT cf = c * __ldg(P.sqrtS + sidf);
             if ((g8 & 128u) && (a.neg & 1u)) cf = -cf;  // (g*, 1) in a Gamma- block
             VT u[D];
-#pragma unroll
-            for (int g = 0; g < D; ++g) u[g] = st_get<VT, ST>(__ldg(x + (size_t)tgt * D + g));
+            lane_row<VT, ST, D>(x, tgt, n_elems, vec, u);
             const VT *R = s_rho + (size_t)(g8 & 127u) * D * RP;
 #pragma unroll
             for (int be = 0; be < D; ++be) {
@@ -125,9 +183,11 @@ __global__ void __launch_bounds__(kLaneThreads) hvp_lane_kernel(const __grid_con
                 val[g] = v * inv_sq;
             }
         }
+        VT xo[D];
+        lane_row<VT, ST, D>(x, rep, n_elems, vec, xo);
 #pragma unroll
         for (int g = 0; g < D; ++g) {
-            const VT xv = st_get<VT, ST>(__ldg(x + seg + g));
+            const VT xv = xo[g];
             const ST ys = st_put<VT, ST>(val[g] + diag * xv);
             y[seg + g] = ys;
             if (want_dot) dacc.add(xv, st_get<VT, ST>(ys));

@@ -147,12 +147,18 @@ def test_real_form_lanczos_and_thermo(name, two_s):
             al, be = [], []
             for r in range(R):
                 ar, br = lanczos(ob.hv, V0[:, r], n_steps)
-                k = len(ar)
-                assert st[r] == k
-                assert np.allclose(a[r, :k], ar, rtol=1e-10, atol=1e-10)
-                assert np.allclose(b[r, :k], br, rtol=1e-10, atol=1e-10)
-                al.append(a[r, :k])
-                be.append(b[r, :k])
+                # a real-form block holds every level kappa times, so the Krylov space is exhausted after
+                # dim / kappa steps at most; past a beta at rounding level the steps are rounding noise
+                # and the two sides' stop tests may fire one step apart: compare the steps before it
+                tiny = np.nonzero(np.abs(br) < 1e-8 * (np.abs(ar).max() + 1.0))[0]
+                kk = len(ar) if len(tiny) == 0 else int(tiny[0]) + 1
+                assert st[r] >= kk and (len(tiny) or st[r] == len(ar))
+                assert np.allclose(a[r, :kk], ar[:kk], rtol=1e-10, atol=1e-10)
+                assert np.allclose(b[r, :kk - 1], br[:kk - 1], rtol=1e-10, atol=1e-10)
+                if len(tiny):  # the exhausting beta is at rounding level on both sides
+                    assert abs(b[r, kk - 1]) < 1e-8 * (np.abs(ar).max() + 1.0)
+                al.append(a[r, :st[r]])
+                be.append(b[r, :st[r]])
             w = int(F.ftlm_group_info(g)["weights"][ir])
             assert w == irr.weight
             gpu_blocks.append(dict(two_M=two_M, d_gamma=w, dim=dim, alpha=a, beta=b, steps=st))
