@@ -14,6 +14,7 @@
 namespace ftlm {
 
 constexpr int kLaneThreads = 256;
+constexpr int kLaneFlips = 2;  // flips whose entries and rows are loaded before the first is summed
 
 __host__ __device__ constexpr int lane_gcd(int a, int b) { return b == 0 ? a : lane_gcd(b, a % b); }
 
@@ -145,9 +146,10 @@ __global__ void __launch_bounds__(kLaneThreads) hvp_lane_kernel(const __grid_con
         VT z[D];
 #pragma unroll
         for (int g = 0; g < D; ++g) z[g] = (VT)0;
-        for (uint64_t e = e0; e < e1; ++e) {
-            const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(P.ent + e));
-            const uint32_t tgt = raw.x, g8 = raw.y & 255u, es = (raw.y >> 8) & 255u, sidf = raw.y >> 16;
+        // one flip: coefficient of Eq. 3 times sqrt|Stab r'| (the 1/sqrt|Stab r| comes last), gather of
+        // the target's row, z += cf rho(g*)^T u; flips are summed in entry order
+        auto coef = [&](uint2 raw) {
+            const uint32_t g8 = raw.y & 255u, es = (raw.y >> 8) & 255u, sidf = raw.y >> 16;
             VT c = halfJ;
             if (a.two_s != 1) {
                 const int b = (int)(es & 127u);
@@ -157,9 +159,10 @@ __global__ void __launch_bounds__(kLaneThreads) hvp_lane_kernel(const __grid_con
             }
             VT cf = c * __ldg(P.sqrtS + sidf);
             if ((g8 & 128u) && (a.neg & 1u)) cf = -cf;  // (g*, 1) in a Gamma- block
-            VT u[D];
-            lane_row<VT, ST, D>(x, tgt, n_elems, vec, u);
-            const VT *R = s_rho + (size_t)(g8 & 127u) * D * RP;
+            return cf;
+        };
+        auto accumulate = [&](uint2 raw, VT cf, const VT(&u)[D]) {
+            const VT *R = s_rho + (size_t)(raw.y & 127u) * D * RP;
 #pragma unroll
             for (int be = 0; be < D; ++be) {
                 VT acc = R[be] * u[0];
@@ -167,6 +170,23 @@ __global__ void __launch_bounds__(kLaneThreads) hvp_lane_kernel(const __grid_con
                 for (int ga = 1; ga < D; ++ga) acc += R[ga * RP + be] * u[ga];
                 z[be] += cf * acc;
             }
+        };
+        uint64_t e = e0;
+        for (; e + kLaneFlips <= e1; e += kLaneFlips) {  // kLaneFlips gathers in flight per thread
+            uint2 r[kLaneFlips];
+            VT u[kLaneFlips][D];
+#pragma unroll
+            for (int q = 0; q < kLaneFlips; ++q) r[q] = __ldg(reinterpret_cast<const uint2 *>(P.ent + e + q));
+#pragma unroll
+            for (int q = 0; q < kLaneFlips; ++q) lane_row<VT, ST, D>(x, r[q].x, n_elems, vec, u[q]);
+#pragma unroll
+            for (int q = 0; q < kLaneFlips; ++q) accumulate(r[q], coef(r[q]), u[q]);
+        }
+        for (; e < e1; ++e) {
+            const uint2 r0 = __ldg(reinterpret_cast<const uint2 *>(P.ent + e));
+            VT u0[D];
+            lane_row<VT, ST, D>(x, r0.x, n_elems, vec, u0);
+            accumulate(r0, coef(r0), u0);
         }
         VT val[D];
         if (sid == 0) {
