@@ -39,6 +39,7 @@ struct alignas(8) HvEntry {
     uint8_t esign;
     uint16_t sid;
 };
+static_assert(sizeof(HvEntry) == 8, "entry tables are read as 8-byte words (two per 16-byte load)");
 
 // Packed set: K blocks of one sector whose rows are interleaved by
 // representative, in lifted coordinates: representative r owns the W = sum_k
