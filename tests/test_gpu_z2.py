@@ -20,7 +20,7 @@ from workloads import cluster, rand_block_vectors
 pytestmark = pytest.mark.gpu
 
 CASES = [("icosahedron", 1), ("icosahedron", 3), ("cuboctahedron", 2), ("tetrahedron", 2), ("ring:6", 2),
-         ("square:4x4", 1)]
+         ("square:4x4", 1), ("chain:8", 1), ("q8", 2), ("complete:7", 2), ("petersen", 1)]
 
 
 @pytest.mark.parametrize("name,two_s", CASES)
@@ -48,7 +48,7 @@ def test_flip_sector_matches_oracle(name, two_s):
     assert np.array_equal(masks[order][:, :W], osec.stab.astype(np.uint64))
     rng = np.random.default_rng(2)
     for k, ir in enumerate(gx.irreps):
-        if ir.rho is None or ir.dim > 5:
+        if ir.rho is None:
             continue
         ob = BlockBasis(osec, k).with_hamiltonian(c.bonds)
         blk = F.ftlm_build_block(sec, k)

@@ -22,7 +22,8 @@ from oracle.group import Group, SpinFlipExtended
 from oracle.sector import block_dims
 from workloads import cluster
 
-CASES = [("icosahedron", 1), ("tetrahedron", 2), ("tetrahedron", 3), ("cuboctahedron", 1), ("ring:6", 2)]
+CASES = [("icosahedron", 1), ("tetrahedron", 2), ("tetrahedron", 3), ("cuboctahedron", 1), ("ring:6", 2),
+         ("chain:6", 2), ("q8", 1), ("complete:5", 2)]  # the last three with real forms of complex/quaternionic irreps
 
 
 def _flip_matrix(labels, n_sites, two_s):
