@@ -262,15 +262,23 @@ __global__ void lzp_finalize(int mode, int j, int K, int B, int grid, const uint
     const int k = t / B, b = t % B;
     const size_t e = ((size_t)p * K + k) * B + b;
     const uint64_t nt = ntile[p], t0 = tile0[p];
-    double sum = 0.0;
-    if (nt >= (uint64_t)grid) {
-        for (int c = 0; c < grid; ++c) sum += part[(((size_t)p * grid + c) * K + k) * B + b];
-    } else {
-        for (uint64_t i = 0; i < nt; ++i) {
-            const int c = (int)((t0 + i) % (uint64_t)grid);
-            sum += part[(((size_t)p * grid + c) * K + k) * B + b];
-        }
+    // the partials of the CTAs that worked on part p, summed in a fixed order: eight interleaved
+    // running sums (independent loads and adds in flight), then a fixed pairwise combination
+    const uint64_t n = nt >= (uint64_t)grid ? (uint64_t)grid : nt;
+    const uint64_t c0 = nt >= (uint64_t)grid ? 0 : t0 % (uint64_t)grid;
+    auto at = [&](uint64_t i) {
+        uint64_t c = c0 + i;
+        if (c >= (uint64_t)grid) c -= (uint64_t)grid;
+        return part[(((size_t)p * grid + c) * K + k) * B + b];
+    };
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    uint64_t i = 0;
+    for (; i + 8 <= n; i += 8) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] += at(i + q);
     }
+    for (int q = 0; i < n; ++i, ++q) acc[q] += at(i);
+    const double sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     const size_t E = (size_t)gridDim.x * K * B;
     if (mode == 0) {
         const double n = sqrt(sum);
