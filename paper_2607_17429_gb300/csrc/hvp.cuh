@@ -798,9 +798,24 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
             }
 
             // 7. sum over flip groups, output rows, <x~, y~>
+            VT *zs = reinterpret_cast<VT *>(stage);  // the staging buffers are idle here
+            // Four flip groups whose partial rows fit in the staging buffers: every lane stores its
+            // rows ([fg][row][b], a group stride of W BT + BT elements keeps the stores conflict-free),
+            // then each lane adds the four partials of W BT / 32 entries in the order the shuffle
+            // butterfly below uses, (z0 + z1) + (z2 + z3), into group 0's slice: the same sums.
+            const int zstride = W * BT + BT;
+            const bool zq = Q == 4 && (size_t)4 * zstride * sizeof(VT) <= (size_t)nbuf * a.stage_elems * sizeof(ST);
+            if (zq) {
 #pragma unroll
-            for (int i = 0; i < W; ++i)
-                for (int w = BT; w < 32; w <<= 1) z[i] += __shfl_xor_sync(kFullMask, z[i], w);
+                for (int i = 0; i < W; ++i) zs[fg * zstride + i * BT + b] = z[i];
+                __syncwarp();
+                for (int e = lane; e < W * BT; e += 32)
+                    zs[e] = (zs[e] + zs[zstride + e]) + (zs[2 * zstride + e] + zs[3 * zstride + e]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < W; ++i)
+                    for (int w = BT; w < 32; w <<= 1) z[i] += __shfl_xor_sync(kFullMask, z[i], w);
+            }
             if (own_on) {
                 if (!mbar_wait_bounded(bar_own, (parity >> kMaxBuf) & 1u, a.wait_limit)) {
                     if (lane == 0) atomicOr(a.err, kErrWaitTimeout);
@@ -812,8 +827,7 @@ __global__ void __launch_bounds__(hvp_max_threads<VT, SH>(), 1) hvp_kernel(const
                 parity ^= 1u << kMaxBuf;
                 pending &= ~(1u << kMaxBuf);
             }
-            VT *zs = reinterpret_cast<VT *>(stage);  // the staging buffers are idle here
-            if (fg == 0) {
+            if (!zq && fg == 0) {
 #pragma unroll
                 for (int i = 0; i < W; ++i) zs[i * BT + b] = z[i];
             }
