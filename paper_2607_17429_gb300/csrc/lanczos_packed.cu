@@ -255,15 +255,21 @@ struct LzState {
 // multiplies the three coefficients, beta_{j+1} = |sigma w| / sigma, and the next
 // scale s_{j+1} = 1 / |sigma w| (v_{j+1} = sigma w / (sigma beta_{j+1})).  Without
 // it sigma = 1 and the recurrence is unchanged.
+// Slices of the partial sums per (block, chain): the CTA of a part has K B x kFinSlices threads.
+constexpr int kFinThreads = 1024;
+__host__ __device__ inline int fin_slices(int KB) { return KB >= kFinThreads ? 1 : (kFinThreads / KB < 8 ? kFinThreads / KB : 8); }
+
 __global__ void lzp_finalize(int mode, int j, int K, int B, int grid, const uint64_t *tile0, const uint64_t *ntile,
                              const double *part, LzState st, double tol, int scaled) {
-    const int p = blockIdx.x, t = threadIdx.x;
-    if (t >= K * B) return;
+    const int p = blockIdx.x, KB = K * B, S = fin_slices(KB);
+    const int t = threadIdx.x % KB, sl = threadIdx.x / KB;
+    __shared__ double sl_sum[kFinThreads];  // [slice][K B]
     const int k = t / B, b = t % B;
     const size_t e = ((size_t)p * K + k) * B + b;
     const uint64_t nt = ntile[p], t0 = tile0[p];
-    // the partials of the CTAs that worked on part p, summed in a fixed order: eight interleaved
-    // running sums (independent loads and adds in flight), then a fixed pairwise combination
+    // The partials of the CTAs that worked on part p, summed in a fixed order: slice sl takes
+    // partials sl, sl + S, ... in four interleaved running sums (loads in flight), the slices are
+    // then added in slice order; the association depends on the partial count only.
     const uint64_t n = nt >= (uint64_t)grid ? (uint64_t)grid : nt;
     const uint64_t c0 = nt >= (uint64_t)grid ? 0 : t0 % (uint64_t)grid;
     auto at = [&](uint64_t i) {
@@ -271,14 +277,25 @@ __global__ void lzp_finalize(int mode, int j, int K, int B, int grid, const uint
         if (c >= (uint64_t)grid) c -= (uint64_t)grid;
         return part[(((size_t)p * grid + c) * K + k) * B + b];
     };
-    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    uint64_t i = 0;
-    for (; i + 8 <= n; i += 8) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] += at(i + q);
+    if (sl < S && t < KB) {
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        uint64_t i = (uint64_t)sl;
+        for (; i + 3 * (uint64_t)S < n; i += 4 * (uint64_t)S) {
+            const double v0 = at(i), v1 = at(i + S), v2 = at(i + 2 * S), v3 = at(i + 3 * S);
+            acc[0] += v0;
+            acc[1] += v1;
+            acc[2] += v2;
+            acc[3] += v3;
+        }
+        if (i < n) acc[0] += at(i);  // at most three left
+        if (i + S < n) acc[1] += at(i + S);
+        if (i + 2 * (uint64_t)S < n) acc[2] += at(i + 2 * S);
+        sl_sum[sl * KB + t] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
-    for (int q = 0; i < n; ++i, ++q) acc[q] += at(i);
-    const double sum = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    __syncthreads();
+    if (sl != 0 || t >= KB) return;
+    double sum = sl_sum[t];
+    for (int q = 1; q < S; ++q) sum += sl_sum[q * KB + t];
     const size_t E = (size_t)gridDim.x * K * B;
     if (mode == 0) {
         const double n = sqrt(sum);
@@ -563,7 +580,7 @@ ftlm_status lanczos_packed_st(const std::vector<LzSetIn> &sets, int R, int n_ste
         ftlm_status s1 = lzp_start_launch<VT, ST>(K, la, lz_grid, stream);
         if (s1 != FTLM_OK) return s1;
         count_launch();
-        lzp_finalize<<<P, K * B, 0, stream>>>(0, 0, K, B, lz_grid, lz_t0, lz_nt, lz_part.p, st, tol, kScaled);
+        lzp_finalize<<<P, K * B * fin_slices(K * B), 0, stream>>>(0, 0, K, B, lz_grid, lz_t0, lz_nt, lz_part.p, st, tol, kScaled);
         FTLM_CUDA(cudaGetLastError());
         // ---- the step loop (captured once on a private stream, replayed once on the caller's)
         const bool prof = profiling_on();
@@ -586,7 +603,7 @@ ftlm_status lanczos_packed_st(const std::vector<LzSetIn> &sets, int R, int n_ste
                     FTLM_CUDA(capture ? cudaEventRecordWithFlags(ev.back(), ss, cudaEventRecordExternal)
                                       : cudaEventRecord(ev.back(), ss));
                 count_launch();
-                lzp_finalize<<<P, K * B, 0, ss>>>(1, j, K, B, hv_grid, hv_t0, hv_nt, hv_part.p, st, tol, kScaled);
+                lzp_finalize<<<P, K * B * fin_slices(K * B), 0, ss>>>(1, j, K, B, hv_grid, hv_t0, hv_nt, hv_part.p, st, tol, kScaled);
                 FTLM_CUDA(cudaGetLastError());
                 LzUpd<VT> U = ua[q];
                 U.has_prev = j > 0;
@@ -594,7 +611,7 @@ ftlm_status lanczos_packed_st(const std::vector<LzSetIn> &sets, int R, int n_ste
                 lzp_update<VT, ST><<<up_grid, kLzThreads, 0, ss>>>(U);
                 FTLM_CUDA(cudaGetLastError());
                 count_launch();
-                lzp_finalize<<<P, K * B, 0, ss>>>(2, j, K, B, up_grid, d_ut.p, d_ut.p + P, up_part.p, st, tol,
+                lzp_finalize<<<P, K * B * fin_slices(K * B), 0, ss>>>(2, j, K, B, up_grid, d_ut.p, d_ut.p + P, up_part.p, st, tol,
                                                   kScaled);
                 FTLM_CUDA(cudaGetLastError());
             }
