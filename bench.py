@@ -319,7 +319,7 @@ def hv_roofline(prof, dtype_name, flips, n_reps, W, B, esize, mode="search",
 
 def _oracle_worker(args):
     """One process of the CPU baseline: label-keyed oracle rows for random representatives (spawned)."""
-    seed, budget_s = args
+    seed, budget_s, name, two_s, B = args
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     sys.path.insert(0, ROOT)
     from oracle import native
@@ -327,7 +327,8 @@ def _oracle_worker(args):
     from oracle.group import Group
     from workloads import cluster, label_keyed_values
 
-    c = cluster(CLUSTER)
+    c = cluster(name)
+    N, d = c.n_sites, two_s + 1
     og = Group(c.gens, c.bonds)
     inv = og.element(c.gens[2])
     ir = [i for i, r in enumerate(og.irreps) if r.dim == 5 and r.chars[inv] > 0][0]  # H_g
@@ -336,33 +337,39 @@ def _oracle_worker(args):
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
         batch = []
-        for _ in range(8):
-            bits = rng.permutation(np.r_[np.ones(15, dtype=np.int64), np.zeros(15, dtype=np.int64)])
-            lab = int(sum(int(v) << k for k, v in enumerate(bits)))
-            batch.append(native.min_rep(30, 2, og.perms, lab)[0])
-        out = hv_rows_by_label(og, ir, c.bonds, 1.0, TWO_S, batch,
-                               lambda lab, n: label_keyed_values([lab], n, R, 1)[0])
+        while len(batch) < 8:  # uniform over the M = 0 product states (rejection on the digit sum)
+            dig = rng.integers(0, d, N)
+            if int(dig.sum()) * 2 != N * two_s:
+                continue
+            lab = int(sum(int(v) * d ** k for k, v in enumerate(dig)))
+            batch.append(native.min_rep(N, d, og.perms, lab)[0])
+        out = hv_rows_by_label(og, ir, c.bonds, 1.0, two_s, batch,
+                               lambda lab, n: label_keyed_values([lab], n, B, 1)[0])
         rows += sum(0 if y is None else y.shape[0] for y in out)
         reps += len(batch)
     return rows, reps, time.perf_counter() - t0
 
 
-def cpu_baseline(budget_s=10.0):
-    """The oracle's H·v (FP64, label-keyed rows of the H_g block, B = 8) on every host core, bounded sample."""
+def cpu_baseline(budget_s=10.0, name=None, two_s=None, B=None):
+    """The oracle's H·v (FP64, label-keyed rows of the H_g block at M = 0) on every host core, bounded sample;
+    the benchmark workload by default."""
     import multiprocessing as mp
 
+    name = name or CLUSTER
+    two_s = two_s or TWO_S
+    B = B or R
     cores = os.cpu_count() or 1
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_worker, [(1000 + i, budget_s) for i in range(cores)])
+        res = pool.map(_oracle_worker, [(1000 + i, budget_s, name, two_s, B) for i in range(cores)])
     wall = time.perf_counter() - t0
     rows = sum(r[0] for r in res)
     reps = sum(r[1] for r in res)
     busy = max(r[2] for r in res)
-    return {"value": rows * R / busy / 1e9, "unit": "Gstates/s", "cores": cores, "kind": "oracle",
-            "sample": f"{reps} random representatives of the H_g block (d=5) of the icosidodecahedron M=0 sector, "
-                      f"B={R} right-hand sides, FP64 label-keyed oracle rows (Eqs. 15-16), {cores} spawned "
+    return {"value": rows * B / busy / 1e9, "unit": "Gstates/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} random representatives of the H_g block (d=5) of the {name} s={two_s}/2 M=0 sector, "
+                      f"B={B} right-hand sides, FP64 label-keyed oracle rows (Eqs. 15-16), {cores} spawned "
                       f"processes x {busy:.1f} s (wall {wall:.1f} s including start-up)"}
 
 
@@ -529,6 +536,8 @@ def config5(args):
     wl5 = "dodecahedron_s3/2_M0_Hg_B1"
     out["roofline"] = hv_roofline(f32["prof"], "f32", 0, out["n_reps"], 5, 1, 4, flips32, wl5)
     out["roofline_f64_search"] = hv_roofline(f64["prof"], "f64", 0, out["n_reps"], 5, 1, 8, "search", wl5)
+    if not args.no_cpu_baseline:  # the oracle on the host cores: sampled rows of the same block, B = 1
+        out["cpu_baseline"] = cpu_baseline(budget_s=10.0, name="dodecahedron", two_s=3, B=1)
     sel = T_GRID >= 0.05
     a32, a64 = f32["thermo"], f64["thermo"]
     out["E0_f32"], out["E0_f64"] = a32[4], a64[4]
