@@ -123,3 +123,43 @@ def test_submit_rejects_bad_jobs():
             assert e.value.status == F.EINVAL
     finally:
         srv.close()
+
+
+def test_real_form_and_wide_irrep_jobs():
+    """Jobs on irreps of complex type (C_12, AGL(1,11)), quaternionic type (Q_8) and of dimension 6 and 10
+    (S_5 on the Petersen graph, AGL(1,11)): in the mix they give the coefficients they give alone, and their
+    info carries the irrep's weight."""
+    torch_cuda()
+    F = ftlm()
+    jobs = []
+    for name, two_s, Ms in (("chain:12", 1, (0, 2)), ("complete:11", 2, (0,)), ("petersen", 2, (0, 2)),
+                            ("q8", 3, (2,))):
+        g = product_group(name)
+        info = F.ftlm_group_info(g)
+        for two_M in Ms:
+            sec = F.ftlm_build_sector(g, two_s, two_M)
+            for ir in range(len(info["dims"])):
+                if info["fs"][ir] == 1 and info["dims"][ir] < 6:
+                    continue  # complex-type real forms and d = 6 only
+                if F.ftlm_basis_info(F.ftlm_build_block(sec, ir))["dim"] < 64:
+                    continue  # Krylov spaces of real-form blocks exhaust at dim / kappa: keep 12 steps below that
+                jobs.append(dict(g=g, two_s=two_s, two_M=two_M, irrep=ir, R=2, n_steps=12,
+                                 block_id=64 * two_M + ir, weight=int(info["weights"][ir])))
+    assert len(jobs) >= 6
+    srv = F.Server(cap_bytes=4 << 30, n_workers=2, max_parts=8)
+    try:
+        ids = [srv.submit(j["g"], j["two_s"], j["two_M"], j["irrep"], j["R"], j["n_steps"], 5, j["block_id"],
+                          F.GAUSS, F.F64) for j in jobs]
+        res = [srv.wait(i, 300.0) for i in ids]
+    finally:
+        srv.close()
+    for j, (info, a, b, st) in zip(jobs, res):
+        blk = F.ftlm_build_basis(j["g"], j["two_s"], j["two_M"], j["irrep"])
+        a1, b1, s1 = F.ftlm_lanczos(blk, F.F64, j["R"], j["n_steps"], 5, j["block_id"], F.GAUSS)
+        assert info["status"] == F.OK and info["d_gamma"] == j["weight"]
+        assert np.array_equal(st, s1)
+        for r in range(j["R"]):
+            k = s1[r]
+            scale = np.abs(a1[r, :k]).max() + 1.0
+            assert np.abs(a[r, :k] - a1[r, :k]).max() <= 1e-10 * scale
+            assert np.abs(b[r, :k] - b1[r, :k]).max() <= 1e-10 * scale
