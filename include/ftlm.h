@@ -184,7 +184,9 @@ void ftlm_sector_free(ftlm_sector *s);
  * (may be NULL) receives the flip count.  From then on every packed H·v and
  * Lanczos call on blocks of this sector reads the table (the same flips in
  * the same order as the search, so the results are bitwise those of the
- * search path).  Synchronises cuda_stream; FTLM_ENOMEM if the table does not
+ * search path; a single block at one right-hand side runs one thread per
+ * representative and sums its flips in entry order, equal to the search path
+ * to rounding).  Synchronises cuda_stream; FTLM_ENOMEM if the table does not
  * fit.  ftlm_sector_free_entries drops the table (back to the search).
  * Neither may run while another call uses the sector.
  */
