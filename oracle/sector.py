@@ -13,7 +13,6 @@
 """
 from __future__ import annotations
 
-import numpy as np
 
 
 def digit_total(n_sites: int, two_s: int, two_M: int) -> int:

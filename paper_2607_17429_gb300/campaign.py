@@ -151,7 +151,7 @@ class LibraryRunner:
 
     def blocks(self) -> list:
         """(2M, irrep) of every block the campaign covers, in run order."""
-        cfg, F = self.cfg, self.F
+        cfg = self.cfg
         if cfg.flip:
             n_ir = 2 * len(self.weights)
             return [(0, k) for k in (cfg.irreps if cfg.irreps is not None else range(n_ir))]

@@ -11,7 +11,7 @@ import scipy.linalg
 from gpu_common import ftlm, product_group
 from helpers import oracle_group
 from oracle.basis import BlockBasis, SectorBasis
-from oracle.lanczos import lanczos, ritz, start_vectors, thermo
+from oracle.lanczos import lanczos, start_vectors, thermo
 from workloads import cluster
 
 pytestmark = pytest.mark.gpu
