@@ -14,7 +14,6 @@
 from __future__ import annotations
 
 
-
 def digit_total(n_sites: int, two_s: int, two_M: int) -> int:
     twice = n_sites * two_s + two_M
     if twice % 2:
