@@ -127,3 +127,36 @@ def test_table_lanczos_one_block_one_chain():
         a1, b1, s1 = F.ftlm_lanczos(blk, F.F64, 1, 30, 3, ir)
         assert np.array_equal(s0, s1)
         assert np.allclose(a0, a1, rtol=1e-11, atol=1e-11) and np.allclose(b0, b1, rtol=1e-11, atol=1e-11)
+
+
+def test_lane_kernel_several_parts():
+    """The one-thread-per-representative kernel with several parts in one launch (every M >= 0 sector of
+    a cluster as single-block sets at R = 1, each sector with its entry table): every set's coefficients
+    match the same set run alone on the search path, to rounding (FP64)."""
+    torch_cuda()
+    F = ftlm()
+    g = product_group("icosahedron")
+    ir = 8  # a five-dimensional irrep
+    sets, secs, ids = [], [], []
+    for two_M in range(0, 14, 2):
+        sec = F.ftlm_build_sector(g, 3, two_M)
+        mb = F.ftlm_build_multiblock(sec, [ir])
+        if F.ftlm_multiblock_info(mb)["dims"][0] < 40:
+            continue
+        sets.append(mb)
+        secs.append(sec)
+        ids.append([64 * two_M + ir])
+    assert len(sets) >= 4
+    alone = []
+    for mb, bid in zip(sets, ids):
+        a0, b0, s0 = F.ftlm_lanczos_multi(mb, F.F64, 1, 25, 9, bid, F.GAUSS)
+        alone.append((a0, b0, s0))
+    for sec in secs:
+        F.ftlm_sector_build_entries(sec)
+    a, b, st = F.ftlm_lanczos_sets(sets, F.F64, 1, 25, 9, ids, F.GAUSS)
+    for i, (a0, b0, s0) in enumerate(alone):
+        assert np.array_equal(st[i], s0)
+        k = int(s0[0, 0])
+        scale = np.abs(a0[0, 0, :k]).max() + 1.0
+        assert np.abs(a[i, 0, 0, :k] - a0[0, 0, :k]).max() <= 1e-10 * scale
+        assert np.abs(b[i, 0, 0, :k] - b0[0, 0, :k]).max() <= 1e-10 * scale
