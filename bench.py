@@ -100,6 +100,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x):
+    """Largest value of x over the ranks of the default process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(states_per_rank, ms_all, world):
+    """Whole-job Gstates/s of `world` replicas that each processed `states_per_rank` in at most ms_all ms."""
+    return states_per_rank * world / (ms_all / 1e3) / 1e9
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -176,12 +194,8 @@ def run_ours(args, rank, world):
 
     with Clocks(dev) as clk:
         ms, states, prof, out = timed(dtype, args.steps, args.warmup)
-    ms_all = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_all = float(t.item())
-    value = states * world / (ms_all / 1e3) / 1e9  # replicas: every rank runs the same workload
+    ms_all = max_over_ranks(ms)  # the slowest replica's time
+    value = replica_value(states, ms_all, world)  # replicas: every rank runs the same workload
     res = {"ms": ms, "states": states, "prof": prof, "out": out, "clocks": clk.summary(), "value": value,
            "ms_all": ms_all}
     # algorithmic counts of one packed H·v launch (for the roofline)
